@@ -1,0 +1,359 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: every check is a printed value of
+the paper (tests/golden), a closed form, a brute-force dense solve on a tiny
+grid, an independent high-precision integration, or an invariant.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import npb_inputs as I
+
+from . import sphere_case
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _golden(name):
+    rows = []
+    with open(os.path.join(HERE, "golden", name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+# --------------------------------------------------------------------------- Eq. (ana3)
+def test_ana3_matches_exact_ode_solution(oracle_lib):
+    """Eq. (ana3) equals the exact flow of alpha w_t = -kbar^2 sinh w:
+    tanh(w(t)/2) = tanh(w0/2) exp(-kbar^2 t / alpha), evaluated in 50-digit arithmetic."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    for w0 in [-700.0, -40.0, -3.2, -0.5, -1e-6, 0.0, 1e-9, 0.3, 2.0, 17.0, 300.0, 1e4]:
+        for kb2tau in [1e-8, 1e-3, 0.05, 1.0, 8.4, 30.0]:
+            a = 0.5 * kb2tau
+            ref = 2 * mp.atanh(mp.tanh(mp.mpf(w0) / 2) * mp.exp(-mp.mpf(kb2tau)))
+            got = oracle_lib.ana3(w0, a)
+            assert abs(got - float(ref)) <= 1e-13 * max(1.0, abs(float(ref))), (w0, kb2tau, got, ref)
+
+
+def test_ana3_against_rk4_integration(oracle_lib):
+    """An independent 40-digit RK4 integration of alpha w_t = -kbar^2 sinh w."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    for w0, kb2, tau in [(3.0, 0.84, 0.4), (-1.5, 2.0, 0.25), (0.7, 1.0, 1.0)]:
+        w = mp.mpf(w0)
+        steps = 4000
+        hstep = mp.mpf(tau) / steps
+        f = lambda x: -kb2 * mp.sinh(x)  # noqa: E731
+        for _ in range(steps):
+            k1 = f(w)
+            k2 = f(w + hstep / 2 * k1)
+            k3 = f(w + hstep / 2 * k2)
+            k4 = f(w + hstep * k3)
+            w = w + hstep / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+        got = oracle_lib.ana3(w0, 0.5 * kb2 * tau)
+        assert abs(got - float(w)) < 1e-12 * max(1, abs(float(w)))
+
+
+def test_ana3_semigroup_oddness_identity(oracle_lib):
+    rng = np.random.default_rng(1)
+    for w in rng.normal(0, 5, 50):
+        a1, a2 = 0.3, 1.7
+        two = oracle_lib.ana3(oracle_lib.ana3(w, a1), a2)
+        one = oracle_lib.ana3(w, a1 + a2)
+        assert abs(two - one) < 1e-12 * max(1, abs(one))
+        assert oracle_lib.ana3(-w, a1) == -oracle_lib.ana3(w, a1)
+        assert abs(oracle_lib.ana3(w, 0.0) - w) < 1e-13 * max(1, abs(w))
+        assert abs(oracle_lib.ana3(w, a1)) <= abs(w)  # the flow is dissipative
+
+
+def test_nonlinear_stage_only_where_kappa_positive(oracle_lib):
+    u = np.linspace(-3, 3, 5 * 6 * 7).reshape(5, 6, 7).copy()
+    k2 = np.zeros_like(u)
+    k2[2, 3, 4] = 0.84
+    k2[0, 0, 0] = 0.84  # a face node: the stage never touches faces
+    before = u.copy()
+    oracle_lib.nonlinear(u, k2, 10.0)
+    changed = np.argwhere(u != before)
+    assert [tuple(c) for c in changed] == [(2, 3, 4)]
+    t = math.tanh(before[2, 3, 4] / 2) * math.exp(-0.84 * 10.0)
+    assert abs(u[2, 3, 4] - 2 * math.atanh(t)) < 1e-13
+
+
+# --------------------------------------------------------------------------- line solves
+def _dense_direction_operator(e_half, direction, r):
+    """Brute force: the full (nodes x nodes) matrix of (1 - tau delta_d^2) on interior nodes,
+    identity on faces (Eq. SpatialOperators).  Built node by node from its definition."""
+    nz, ny, nx = e_half.shape
+    shape = (nz, ny, nx)
+    n = nx * ny * nz
+    M = np.zeros((n, n))
+    stride = [1, nx, nx * ny][direction]
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                p = (k * ny + j) * nx + i
+                if i in (0, nx - 1) or j in (0, ny - 1) or k in (0, nz - 1):
+                    M[p, p] = 1.0
+                    continue
+                ep = e_half.reshape(-1)[p]
+                em = e_half.reshape(-1)[p - stride]
+                M[p, p] = 1.0 + r * (ep + em)
+                M[p, p + stride] = -r * ep
+                M[p, p - stride] = -r * em
+    return M, shape
+
+
+@pytest.mark.parametrize("direction", [0, 1, 2])
+def test_sweep_equals_dense_solve(oracle_lib, direction):
+    rng = np.random.default_rng(10 + direction)
+    nz, ny, nx = 6, 7, 5
+    e_half = np.ascontiguousarray(rng.choice([1.0, 80.0, 160.0 / 81.0], size=(nz, ny, nx)))
+    u = np.ascontiguousarray(rng.normal(0, 10, (nz, ny, nx)))
+    tau, h = 0.37, 0.5
+    r = tau / h / h
+    M, shape = _dense_direction_operator(e_half, direction, r)
+    ref = np.linalg.solve(M, u.reshape(-1)).reshape(shape)
+    got = u.copy()
+    oracle_lib.sweep(got, e_half, direction, tau, h)
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+    # faces untouched
+    faces = np.ones_like(u, dtype=bool)
+    faces[1:-1, 1:-1, 1:-1] = False
+    assert np.array_equal(got[faces], u[faces])
+
+
+def test_lodie2_step_equals_dense_brute_force(oracle_lib):
+    """One LODIE2 step S, X, Y, Z, N on a 7x6x5 grid against dense inverses."""
+    rng = np.random.default_rng(3)
+    nz, ny, nx = 5, 6, 7
+    tau, h = 2.5, 0.5
+    eps_node = rng.choice([1.0, 80.0], size=(nz, ny, nx)).astype(float)
+    ex, ey, ez = oracle_lib.eps_half_harmonic(eps_node)
+    k2 = np.where(eps_node > 1, 0.84, 0.0)
+    rho = np.zeros((nz, ny, nx))
+    rho[2, 3, 3] = 5000.0
+    rho[1, 2, 4] = -300.0
+    st = oracle_lib.Setup(None, None, rho, eps_node, k2, (ex, ey, ez), None)
+    u0 = rng.normal(0, 3, (nz, ny, nx))
+    got = u0.copy()
+    oracle_lib.lod_run(got, st, tau, h, 1, scheme=oracle_lib.LODIE2)
+
+    r = tau / h / h
+    interior = np.zeros_like(u0, dtype=bool)
+    interior[1:-1, 1:-1, 1:-1] = True
+    w = u0 + tau * rho * interior
+    for d, e in enumerate((ex, ey, ez)):
+        M, shape = _dense_direction_operator(e, d, r)
+        w = np.linalg.solve(M, w.reshape(-1)).reshape(shape)
+    t = np.tanh(w / 2) * np.exp(-k2 * tau)
+    ref = np.where(interior & (k2 > 0), 2 * np.arctanh(t), w)
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_linear_fixed_point_equals_direct_solve(oracle_lib):
+    """kbar = 0: the LOD iteration converges to the fixed point of u = Z Y X (u + tau rho),
+    which a direct dense solve gives without any time stepping."""
+    rng = np.random.default_rng(5)
+    nz = ny = nx = 7
+    tau, h = 0.8, 0.5
+    eps_node = np.where(rng.random((nz, ny, nx)) < 0.4, 1.0, 80.0)
+    eh = oracle_lib.eps_half_harmonic(eps_node)
+    rho = np.zeros((nz, ny, nx))
+    rho[3, 3, 3] = 400.0
+    rho[2, 4, 3] = -150.0
+    u = np.zeros((nz, ny, nx))
+    u[0] = 1.0
+    u[:, :, -1] = -0.5
+    st = oracle_lib.Setup(None, None, rho, eps_node, np.zeros_like(u), eh, None)
+    r = tau / h / h
+    Ms = [_dense_direction_operator(e, d, r)[0] for d, e in enumerate(eh)]
+    K = np.linalg.solve(Ms[2], np.linalg.solve(Ms[1], np.linalg.inv(Ms[0])))
+    inner = np.zeros_like(u, dtype=bool)
+    inner[1:-1, 1:-1, 1:-1] = True
+    I_ = inner.reshape(-1)
+    B_ = ~I_
+    KII = K[np.ix_(I_, I_)]
+    rhs = KII @ (tau * rho.reshape(-1)[I_]) + K[np.ix_(I_, B_)] @ u.reshape(-1)[B_]
+    fixed = np.linalg.solve(np.eye(KII.shape[0]) - KII, rhs)
+    got = u.copy()
+    oracle_lib.lod_run(got, st, tau, h, 3000, scheme=oracle_lib.LODIE2)
+    assert np.max(np.abs(got.reshape(-1)[I_] - fixed)) <= 1e-10 * np.max(np.abs(fixed))
+
+
+# --------------------------------------------------------------------------- set-up
+def test_mask_matches_lattice_ball_count(oracle_lib):
+    """Born set-up: nodes on/inside |r| <= R are exactly the lattice points i^2+j^2+k^2 <= (R/h)^2."""
+    p = I.born_sphere(0.0, n=33, h=0.5, radius=2.0)
+    m = oracle_lib.mask_vdw(p)
+    c = 16
+    k, j, i = np.meshgrid(*(np.arange(33) - c,) * 3, indexing="ij")
+    ref = (i * i + j * j + k * k <= 16).astype(np.uint8)
+    assert np.array_equal(m, ref)
+    assert int(ref.sum()) == 257  # lattice points in a ball of radius 4
+
+
+def test_charge_spread_moments(oracle_lib):
+    """Trilinear spreading preserves total charge and the dipole moment exactly."""
+    p = I.random_walk_molecule(60, 65, 0.5, seed=77)
+    qt = oracle_lib.charge_spread(p)
+    nz, ny, nx = qt.shape
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    assert abs(qt.sum() - p.q.sum()) < 1e-12
+    for d, idx in enumerate((i, j, k)):
+        node_x = p.origin[d] + p.h * idx
+        assert abs((qt * node_x).sum() - (p.q * p.xyz[:, d]).sum()) < 1e-10
+    assert np.count_nonzero(qt) <= 8 * p.n_atoms
+
+
+def test_boundary_properties(oracle_lib):
+    """Eq. (BoundaryCond): superposition, Coulomb limit, and the screened decay ratio."""
+    base = I.born_sphere(0.84, n=17, h=0.5)
+    u1 = np.zeros(oracle_lib.grid_shape(base))
+    oracle_lib.boundary(base, oracle_lib.SOLVENT, u1)
+    # face-centre node sits 4 A from the charge; a corner node sits 4*sqrt(3) A away
+    C = oracle_lib.C_BJERRUM
+    d_face, d_corner = 4.0, 4.0 * math.sqrt(3.0)
+    kap = math.sqrt(0.84 / 80.0)
+    ratio = u1[8, 8, 0] / u1[0, 0, 0]
+    assert abs(ratio - (d_corner / d_face) * math.exp(-kap * (d_face - d_corner))) < 1e-12
+    vac = np.zeros_like(u1)
+    oracle_lib.boundary(base, oracle_lib.VACUUM, vac)
+    assert abs(vac[8, 8, 0] * d_face - C) < 1e-9 * C  # eps_in = 1, q = 1
+    # superposition over atoms
+    two = I.Problem(xyz=np.array([[0.3, -0.2, 0.1], [-0.4, 0.5, 0.2]]), q=np.array([0.7, -0.3]),
+                    radius=np.array([1.5, 1.8]), eps_in=1.0, eps_out=80.0, kappa2=0.84, h=0.5,
+                    n=(17, 17, 17), origin=base.origin)
+    parts = []
+    for a in range(2):
+        one = I.Problem(xyz=two.xyz[a:a + 1], q=two.q[a:a + 1], radius=two.radius[a:a + 1],
+                        eps_in=1.0, eps_out=80.0, kappa2=0.84, h=0.5, n=(17, 17, 17), origin=base.origin)
+        ua = np.zeros_like(u1)
+        oracle_lib.boundary(one, oracle_lib.SOLVENT, ua)
+        parts.append(ua)
+    both = np.zeros_like(u1)
+    oracle_lib.boundary(two, oracle_lib.SOLVENT, both)
+    assert np.allclose(both, parts[0] + parts[1], rtol=1e-13, atol=1e-13)
+
+
+# --------------------------------------------------------------------------- the paper's example
+@pytest.mark.parametrize("h", [1.0, 0.5, 0.25, 0.125])
+def test_paper_table2_sphere_errors(oracle_lib, h):
+    """Table 2 (LODIE rows): the sphere benchmark reproduces the printed relative errors."""
+    rows = {float(r[0]): (float(r[1]), float(r[2])) for r in _golden("paper_table2_lodie.txt")}
+    (l2, linf), _ = sphere_case.run(h)
+    ref_l2, ref_linf = rows[h]
+    # printed to three digits; h = 1 (a 7^3 grid) only to within a few percent
+    tol = 0.04 if h == 1.0 else 0.006
+    assert abs(l2 - ref_l2) <= tol * ref_l2, (h, l2, ref_l2)
+    assert abs(linf - ref_linf) <= tol * ref_linf, (h, linf, ref_linf)
+
+
+def test_paper_lodie1_equals_lodie2_on_sphere(oracle_lib):
+    """Sec. 4.3/4.4: LODIE1 and LODIE2 give the same printed errors on the sphere."""
+    (a2, ai), _ = sphere_case.run(0.5, scheme=1)
+    (b2, bi), _ = sphere_case.run(0.5, scheme=2)
+    assert f"{a2:.2e}" == f"{b2:.2e}" and f"{ai:.2e}" == f"{bi:.2e}"
+
+
+@pytest.mark.parametrize("H", [1.0, 20.0])
+def test_paper_table1_lod_stable_at_dt5(oracle_lib, H):
+    """Table 1: LOD stays finite up to dt = 5 with T = 1e4 dt (h = 0.5, H = 1 and 20)."""
+    rows = _golden("paper_table1_stability.txt")
+    assert any(r[0] == "LOD" and float(r[1]) == H and float(r[4]) == 5.0 for r in rows)
+    (l2, linf), u = sphere_case.run(0.5, dt=5.0, n_steps=10000, H=H)
+    assert np.all(np.isfinite(u)) and math.isfinite(l2) and l2 < 10.0
+
+
+def test_first_order_in_time(oracle_lib):
+    """Remark 3.1: first order in time.  Successive halvings of dt at fixed T shrink the
+    change by a factor close to 2 (Cauchy ratio), as in Table 6."""
+    us = [sphere_case.run(0.5, dt=dt, T=2.0)[1] for dt in (0.02, 0.01, 0.005)]
+    ratio = np.linalg.norm(us[0] - us[1]) / np.linalg.norm(us[1] - us[2])
+    assert 1.6 < ratio < 2.6, ratio
+
+
+# --------------------------------------------------------------------------- Born ion
+def _born_closed_form(q, R, eps_in, eps_out):
+    # classical Born energy, kcal/mol: -(332.0637 q^2 / 2R) (1/eps_in - 1/eps_out)
+    return -0.5 * 332.0637 * q * q / R * (1.0 / eps_in - 1.0 / eps_out)
+
+
+def test_born_energy_converges_in_h(oracle_lib):
+    """kappa = 0 Born ion: the converged RE+V energy approaches the closed form as h -> 0,
+    with at least first-order decay of the error (Sec. 6, first-order convergence)."""
+    ref = _born_closed_form(1.0, 2.0, 1.0, 80.0)
+    assert abs(ref - (-81.978)) < 1e-3
+    errs = []
+    for n, h in [(33, 0.5), (65, 0.25)]:
+        p = I.born_sphere(0.0, n=n, h=h)
+        dg = oracle_lib.energy(p, 0.1, 2000, richardson=True)
+        errs.append(abs(dg - ref) / abs(ref))
+    assert errs[0] < 0.05 and errs[1] < 0.015
+    assert errs[0] / errs[1] > 2.0
+
+
+def test_born_mirror_symmetry_and_energy_linearity(oracle_lib):
+    p = I.born_sphere(0.84, n=17, h=0.5)
+    dg_re, legs, st = oracle_lib.energy(p, 0.5, 40, richardson=True, return_legs=True)
+    u = legs["solvent_tau"]
+    for ax in range(3):
+        assert np.allclose(u, np.flip(u, axis=ax), rtol=0, atol=1e-10 * np.abs(u).max())
+    # (no axis-permutation symmetry: the x, y, z sweep order of the splitting breaks it)
+    # Eq. (rich) is linear, so the RE energy is 2 dG(tau/2) - dG(tau)
+    d_half = oracle_lib.delta_g(st.qt, legs["solvent_half"], legs["vacuum_half"])
+    d_full = oracle_lib.delta_g(st.qt, legs["solvent_tau"], legs["vacuum_tau"])
+    assert abs(dg_re - (2 * d_half - d_full)) < 1e-10 * abs(dg_re)
+
+
+def test_constant_field_is_preserved(oracle_lib):
+    """No source, kbar = 0, constant Dirichlet data: every sweep keeps the constant."""
+    rng = np.random.default_rng(8)
+    eps_node = rng.choice([1.0, 80.0], size=(6, 7, 8))
+    eh = oracle_lib.eps_half_harmonic(eps_node)
+    u = np.full((6, 7, 8), 2.5)
+    st = oracle_lib.Setup(None, None, np.zeros_like(u), eps_node, np.zeros_like(u), eh, None)
+    oracle_lib.lod_run(u, st, 3.0, 0.5, 5)
+    assert np.allclose(u, 2.5, rtol=0, atol=1e-13)
+
+
+def test_sweep_maximum_principle(oracle_lib):
+    """Each line matrix is an M-matrix with unit row sums on faces: no new extrema."""
+    rng = np.random.default_rng(9)
+    eps_node = rng.choice([1.0, 80.0], size=(9, 8, 7))
+    eh = oracle_lib.eps_half_harmonic(eps_node)
+    u = rng.uniform(-1, 2, (9, 8, 7))
+    for d in range(3):
+        v = u.copy()
+        oracle_lib.sweep(v, eh[d], d, 4.0, 0.5)
+        assert v.max() <= u.max() + 1e-12 and v.min() >= u.min() - 1e-12
+
+
+def test_lod_steady_state_tends_to_discrete_npb_solution(oracle_lib):
+    """The LOD steady state carries an O(tau) splitting error (Sec. 3.1): against the
+    explicit-Euler steady state of the unsplit discrete equation the error halves with
+    tau, and Richardson extrapolation (Eq. rich) removes most of it."""
+    p = I.Problem(xyz=np.array([[3.2, 4.1, 3.9], [5.0, 4.0, 4.2], [4.0, 5.2, 3.1]]),
+                  q=np.array([0.6, -0.4, 0.3]), radius=np.array([1.6, 1.8, 1.5]), eps_in=1.0,
+                  eps_out=80.0, kappa2=0.84, h=0.5, n=(17, 17, 17), origin=(0.0, 0.0, 0.0))
+    st = oracle_lib.setup(p, oracle_lib.SOLVENT)
+    T = 20.0
+    ue = st.u0.copy()
+    tau_e = 2.5e-4  # tau * 12 eps_max / h^2 < 1: the explicit scheme stays monotone
+    oracle_lib.euler_run(ue, st, tau_e, 0.5, int(round(T / tau_e)))
+    assert np.all(np.isfinite(ue))
+    legs = {}
+    for tau in (0.02, 0.01):
+        u = st.u0.copy()
+        oracle_lib.lod_run(u, st, tau, 0.5, int(round(T / tau)))
+        legs[tau] = u
+    e1 = np.abs(legs[0.02] - ue).max()
+    e2 = np.abs(legs[0.01] - ue).max()
+    ere = np.abs(2 * legs[0.01] - legs[0.02] - ue).max()
+    assert 1.75 < e1 / e2 < 2.25, (e1, e2)
+    assert ere < 0.15 * e2
