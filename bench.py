@@ -1,0 +1,420 @@
+#!/usr/bin/env python
+"""Throughput of the LODIE2 RE+V solve on GB300 (LOD Mpoint-steps/s).
+
+Workload (default): the 1,000-atom random-walk molecule on a 129^3 grid at h = 0.5 A,
+eps 1/80, kbar^2 = 0.84 A^-2, LODIE2 with dt = 0.4, alpha = 1/25, 25 steps, Richardson
+extrapolation (dt/2 leg: 50 steps) and the LOD vacuum legs: 127^3 x 150 interior
+point-steps per solve.  Sweeps in FP32, combination and energy in FP64; the plain
+FP64 path is timed beside it.
+
+One "step" is one complete solve of that molecule with its atoms resident in HBM: the
+set-up kernels (mask, charge list, face data), the four legs, and the energy reduction
+with its 8-byte read-back.  Steps are timed with CUDA events on the solver's stream;
+L2 is flushed (a 256 MB write) before every step, outside the event pair.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) every rank solves its own copy (weak scaling, no collective on
+the data path); rank 0 prints the line with the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "LOD Mpoint-steps/s"
+UNIT = "Mpoint-steps/s"
+DT, ALPHA, NSTEPS = 0.4, 1.0 / 25.0, 25
+
+
+def workload(name: str):
+    import npb_inputs as I
+
+    if name == "protein_1k":
+        return I.protein_1k(), dict(dt=DT, alpha=ALPHA, n=NSTEPS)
+    if name == "large_20k":
+        return I.large_20k(), dict(dt=DT, alpha=ALPHA, n=40)
+    if name == "born":
+        return I.born_sphere(0.84), dict(dt=0.1, alpha=1.0, n=200)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def point_steps(problem, n: int) -> int:
+    nx, ny, nz = problem.n
+    return (nx - 2) * (ny - 2) * (nz - 2) * n * 6  # (n + 2n) steps x 2 media
+
+
+# ----------------------------------------------------------------------------- distributed
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def aggregate(local_seconds: float, local_units: float, world: int, group=None):
+    """Job-level (max seconds over ranks, total units over ranks) for weak-scaled ranks."""
+    if world <= 1:
+        return local_seconds, local_units
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend(group) == "nccl" else "cpu"
+    t = torch.tensor([local_seconds], dtype=torch.float64, device=dev)
+    u = torch.tensor([local_units], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM, group=group)
+    return float(t.item()), float(u.item())
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu)], stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    """The oracle (plain FP64 C, OpenMP over lines) on the host cores, same metric."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    problem, w = workload(args.workload)
+    n = w["n"]
+    frac = 1.0 if args.workload != "large_20k" else 0.125  # bounded sample of the leg steps
+    n_s = max(1, int(round(n * frac)))
+    units = point_steps(problem, n_s)
+    for _ in range(args.warmup):
+        oracle.energy(problem, w["dt"] / w["alpha"], n_s)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.energy(problem, w["dt"] / w["alpha"], n_s)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = units * args.steps / total / 1e6
+    sample = (f"{args.workload}: one full RE+V solve per step" if frac == 1.0 else
+              f"{args.workload}: RE+V solve with {n_s} of {n} steps per leg pair per step")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- our arm
+def cpu_baseline(problem, w, budget_s: float = 12.0):
+    import oracle
+
+    oracle.build()
+    oracle.set_threads(os.cpu_count() or 1)
+    n = w["n"]
+    # a bounded sample: the full RE+V solve, or fewer steps if one solve would run too long
+    nx, ny, nz = problem.n
+    est_rate = 8e7 * oracle.get_threads()  # conservative oracle point-steps/s
+    n_s = n
+    while n_s > 1 and point_steps(problem, n_s) / est_rate > budget_s:
+        n_s = max(1, n_s // 2)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        oracle.energy(problem, w["dt"] / w["alpha"], n_s)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el > budget_s / 2 or reps >= 3:
+            break
+    value = point_steps(problem, n_s) * reps / el / 1e6
+    return {"value": value, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": f"{reps} RE+V solve(s) of the same molecule with {n_s} steps per dt leg"}
+
+
+def _kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("sweep_kernel.cuh", "sweep_launch.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1410_2788_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def roofline_traffic(kernel: str, workload: str):
+    """ncu DRAM bytes per launch, if a capture of the current kernel source is on file."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    e = d.get(f"{workload}/{kernel}")
+    if not e or e.get("source_hash") != _kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import paper_1410_2788_gb300 as npb
+    from paper_1410_2788_gb300 import build
+
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    npb.load_library()
+
+    problem, w = workload(args.workload)
+    units_per_step = point_steps(problem, w["n"])
+    prec = npb.NPB_FP32_SWEEP if args.precision == "fp32" else npb.NPB_FP64
+    stream = torch.cuda.Stream()
+    ctx = npb.npb_ctx_create(local, 0)
+    npb.npb_ctx_set_stream(ctx, stream.cuda_stream)
+    grid = npb.npb_grid_create(ctx, problem)
+    opts = npb.make_opts(w["dt"], w["alpha"], w["n"], precision=prec)
+    opts64 = npb.make_opts(w["dt"], w["alpha"], w["n"], precision=npb.NPB_FP64)
+    tuning = npb.npb_autotune(grid, opts, reps=5) if args.autotune else []
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step(o):
+        npb.npb_grid_refresh(grid)
+        return npb.npb_energy(grid, o)
+
+    def timed(o, k):
+        ms = []
+        dg = None
+        with torch.cuda.stream(stream):
+            for _ in range(k):
+                flush.zero_()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                dg = step(o)
+                b.record(stream)
+                ms.append((a, b))
+            torch.cuda.synchronize()
+        return [x.elapsed_time(y) for x, y in ms], dg
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            step(opts)
+            step(opts64)
+    torch.cuda.synchronize()
+
+    # ---- headline: K steps of the FP32-sweep path
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    wall0 = time.perf_counter()
+    step_ms, dg = timed(opts, args.steps)
+    wall = time.perf_counter() - wall0
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    total_s, total_units = aggregate(sum(step_ms) / 1e3, units_per_step * args.steps, world)
+    value = total_units / total_s / 1e6
+
+    # ---- the plain FP64 path on the same molecule
+    k64 = max(3, args.steps // 2)
+    ms64, dg64 = timed(opts64, k64)
+    t64, u64 = aggregate(sum(ms64) / 1e3, units_per_step * k64, world)
+
+    # ---- per-kernel times (events around every launch, no graph) for the roofline
+    npb.npb_ctx_profile(ctx, True)
+    kp = max(2, min(5, args.steps))
+    with torch.cuda.stream(stream):
+        for _ in range(kp):
+            flush.zero_()
+            step(opts)
+    torch.cuda.synchronize()
+    stats = npb.npb_ctx_kernel_stats(ctx)
+    npb.npb_ctx_profile(ctx, False)
+    mine = {k: v for k, v in stats.items() if v["launches"] > 0}
+    launches_per_step = sum(v["launches"] for v in mine.values()) / kp
+    dom = max(mine, key=lambda k: mine[k]["ms"])
+    nx, ny, nz = problem.n
+    interior = (nx - 2) * (ny - 2) * (nz - 2)
+    elem = 4 if prec == npb.NPB_FP32_SWEEP else 8
+    if dom.startswith("sweep"):
+        # per launch: read + write of every interior node of every leg in the launch;
+        # a step launches n sweeps over 4 legs and n over 2 legs
+        bytes_per_step = 2 * elem * interior * (4 * w["n"] + 2 * w["n"])
+        launches = mine[dom]["launches"] / kp
+        alg_per_launch = bytes_per_step / launches
+    else:
+        alg_per_launch = float("nan")
+    avg_ms = mine[dom]["ms"] / mine[dom]["launches"]
+    achieved = alg_per_launch / (avg_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind,
+                "traffic": roofline_traffic(dom, args.workload),
+                "alg_bytes_per_launch": alg_per_launch, "avg_launch_ms": avg_ms,
+                "kernel_share": {k: round(v["ms"] / sum(x["ms"] for x in mine.values()), 4) for k, v in mine.items()}}
+
+    # ---- end to end through the C ABI from pinned host buffers
+    pin = {}
+    for k in ("xyz", "q", "radius"):
+        t = torch.from_numpy(np.ascontiguousarray(getattr(problem, k), dtype=np.float64)).pin_memory()
+        pin[k] = t.numpy()
+
+    class HostProblem:
+        pass
+
+    hp = HostProblem()
+    for k in ("eps_in", "eps_out", "kappa2", "h", "n", "origin"):
+        setattr(hp, k, getattr(problem, k))
+    hp.xyz, hp.q, hp.radius = pin["xyz"], pin["q"], pin["radius"]
+    ke = max(3, args.steps // 2)
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            g2 = npb.npb_grid_create(ctx, hp)
+            npb.npb_energy(g2, opts)
+            npb.npb_grid_destroy(g2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            g2 = npb.npb_grid_create(ctx, hp)
+            npb.npb_energy(g2, opts)
+            npb.npb_grid_destroy(g2)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+    te, ue = aggregate(te, units_per_step * ke, world)
+    h2d = sum(pin[k].nbytes for k in pin)
+
+    npb.npb_grid_destroy(grid)
+    npb.npb_ctx_destroy(ctx)
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    base = cpu_baseline(problem, w) if world == 1 else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == npb.NPB_FP32_SWEEP else "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload} (LODIE2 RE+V, {nx}x{ny}x{nz}, {problem.n_atoms} atoms, "
+                               f"dt={w['dt']}, alpha={w['alpha']:.4g}, {w['n']}+{2 * w['n']} steps x 2 media)",
+                   "grid": [nx, ny, nz], "atoms": problem.n_atoms, "energy_dtype": "f64",
+                   "point_steps_per_step": units_per_step, "l2": "flushed (256 MB write) before every step",
+                   "step": "set-up kernels + 4 legs + FP64 energy + 8-byte read-back",
+                   "parallelism": f"replicas x{world}"},
+        "dG_kcal_mol": dg,
+        "solves_per_s": args.steps * world / total_s,
+        "fp64_path": {"value": u64 / t64 / 1e6, "unit": UNIT, "ms_per_step": 1e3 * t64 / k64,
+                      "solves_per_s": k64 * world / t64, "dG_kcal_mol": dg64},
+        "wall_s_timed_region": wall,
+        "roofline": roofline,
+        "cpu_baseline": base,
+        "e2e": {"value": ue / te / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8,
+                "call": "npb_grid_create + npb_energy + npb_grid_destroy from pinned host arrays"},
+        "gpu_launches": int(round(launches_per_step * args.steps)),
+        "clocks": clk,
+        "autotune": tuning[:0] if not args.verbose else tuning,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="protein_1k", choices=["protein_1k", "large_20k", "born"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false")
+    ap.add_argument("--verbose", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

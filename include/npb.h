@@ -1,0 +1,219 @@
+/*
+ * npb.h -- C ABI of the GB300 LOD solver for the time-dependent nonlinear
+ * Poisson-Boltzmann (NPB) equation (Wilson & Zhao, arXiv 1410.2788).
+ *
+ * The solver integrates the pseudo-time NPB equation of Sec. 2.2,
+ *     alpha u_t = div(eps grad u) - kbar^2 sinh(u) + rho_m,            Eq. (TimeDepNPB)
+ * with the locally-one-dimensional implicit-Euler splitting LODIE2 of Sec. 3.1:
+ *     S:  u += tau Q                                                   Eq. (LODIE1_5)
+ *     X, Y, Z:  (1 - tau delta_d^2) v = w, one tridiagonal system per grid line,
+ *               eps taken at half points                              Eqs. (LODIE1_2)-(LODIE1_4),
+ *                                                                      (SpatialOperators)
+ *     N:  analytic flow of alpha w_t = -kbar^2 sinh w                  Eq. (ana3)
+ * with tau = dt/alpha, and computes the electrostatic solvation energy with
+ * the Richardson extrapolation of Eq. (rich) and the LOD vacuum recovery of
+ * Eq. (deltaG3) (Sec. 5.3, "LODIE2 RE+V").
+ *
+ * Units follow Sec. 2.1: lengths in Angstrom, charges in e_c, the potential u
+ * dimensionless (e_c phi / k_B T at 298 K); energies in kcal/mol.
+ *
+ * Conventions (every call):
+ *   - Return codes: NPB_OK (0), NPB_PENDING (1), or a negative NPB_E* code.  On a
+ *     negative code npb_last_error() gives a message (thread-local) and no output
+ *     argument has been written.
+ *   - Ownership: every input pointer is read during the call only; the library
+ *     copies what it keeps.  Handles are freed by their destroy call.  Host
+ *     buffers are plain CPU memory (pinned or pageable).
+ *   - Threads: npb_submit / npb_poll are thread-safe.  All other calls on one
+ *     grid must not run concurrently with each other.
+ *   - Device: the library allocates its own device memory on the context's
+ *     device and launches on the context's stream; there is no CPU fallback.
+ */
+#ifndef NPB_H
+#define NPB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---------------------------------------------------------------- */
+#define NPB_OK 0
+#define NPB_PENDING 1       /* npb_poll: the request has not finished yet            */
+#define NPB_EINVAL (-1)     /* invalid argument (sizes, signs, atoms off the grid)    */
+#define NPB_ENOMEM (-2)     /* over the context's HBM budget or cudaMalloc failed     */
+#define NPB_ECUDA (-3)      /* a CUDA call failed                                     */
+#define NPB_ETIMEOUT (-4)   /* a bounded wait expired (poll timeout, device wait)      */
+#define NPB_ENOTFOUND (-5)  /* unknown ticket                                         */
+#define NPB_ESHUTDOWN (-6)  /* the context is shutting down                           */
+
+/* ---- enums ------------------------------------------------------------------------- */
+#define NPB_SOLVENT 0       /* eps_out outside the molecule, kbar^2 in solvent          */
+#define NPB_VACUUM 1        /* eps_in everywhere, kbar = 0 (the vacuum leg of Eq. deltaG3) */
+
+#define NPB_LODIE2 2        /* S, X, Y, Z, N  (Sec. 3.1; the paper's chosen scheme)     */
+#define NPB_LODIE1 1        /* N, X, Y, Z, S                                            */
+
+#define NPB_FP64 0          /* every stage in FP64                                      */
+#define NPB_FP32_SWEEP 1    /* potential stored and swept in FP32; energy in FP64       */
+
+#define NPB_EPS_HARMONIC 0  /* eps at a half point = harmonic mean of its two nodes     */
+#define NPB_EPS_MIDPOINT 1  /* eps at a half point decided by the half point's location */
+
+/* Legs of one RE+V solve, in the order npb_potential() and npb_apply() name them. */
+#define NPB_LEG_SOLVENT_TAU 0
+#define NPB_LEG_SOLVENT_HALF 1
+#define NPB_LEG_VACUUM_TAU 2
+#define NPB_LEG_VACUUM_HALF 3
+
+/* Single stages for npb_apply() (row-level checks of one LOD stage). */
+#define NPB_OP_SOURCE 0     /* u += tau Q at interior charge nodes        Eq. (LODIE1_5) */
+#define NPB_OP_SWEEP_X 1    /* x line solves                               Eq. (LODIE1_2) */
+#define NPB_OP_SWEEP_Y 2    /* y line solves                               Eq. (LODIE1_3) */
+#define NPB_OP_SWEEP_Z 3    /* z line solves                               Eq. (LODIE1_4) */
+#define NPB_OP_NONLINEAR 4  /* analytic sinh stage at solvent nodes        Eq. (ana3)     */
+#define NPB_OP_STEP 5       /* one full LOD step of opts->scheme                         */
+
+/* What npb_grid_export() copies out (dense nz*ny*nx arrays, x fastest). */
+#define NPB_EXPORT_MASK 0        /* uint8: 1 on/inside the molecular surface            */
+#define NPB_EXPORT_QTILDE 1      /* double: trilinear node charges, e_c                 */
+#define NPB_EXPORT_U0_SOLVENT 2  /* double: Eq. (BoundaryCond) faces, zero interior     */
+#define NPB_EXPORT_U0_VACUUM 3   /* double: Coulomb faces with eps_in, zero interior    */
+
+/* ---- types ------------------------------------------------------------------------- */
+typedef struct npb_ctx npb_ctx;    /* device, stream, HBM budget, serving scheduler   */
+typedef struct npb_grid npb_grid;  /* one molecule's device arrays and leg states      */
+
+/* The problem statement of Sec. 2.1 on the uniform grid of Sec. 3:
+ * atoms r_j (xyz, 3*n_atoms doubles, A), partial charges q_j (e_c), radii (A; the
+ * molecule Omega_m is the union of the closed balls, standing in for an MSMS
+ * surface), eps_in = eps_m and eps_out = eps_s, kappa2 = kbar^2 in A^-2 (solvent
+ * only), grid spacing h (A) and node counts n = (nx, ny, nz), each >= 3.
+ * Node (i, j, k) sits at origin + h (i, j, k).  Every atom's 8-node charge stencil
+ * must lie in the interior (indices 1 .. n-2), else NPB_EINVAL. */
+typedef struct {
+    int32_t n_atoms;
+    const double *xyz;
+    const double *q;
+    const double *radius;
+    double eps_in, eps_out, kappa2, h;
+    int32_t n[3];
+    double origin[3];
+} npb_problem;
+
+/* Pseudo-time options: tau = dt/alpha; the Richardson leg uses dt/2 and 2 n_steps
+ * (Sec. 5.3).  richardson and vacuum_recovery are 0/1 flags; npb_energy() needs
+ * vacuum_recovery = 1 (the FFT vacuum potential of Eq. deltaG2 is not provided). */
+typedef struct {
+    double dt, alpha;
+    int32_t n_steps;
+    int32_t scheme;           /* NPB_LODIE2 (default) or NPB_LODIE1                   */
+    int32_t richardson;       /* 1: RE of Eq. (rich)                                   */
+    int32_t vacuum_recovery;  /* 1: LOD vacuum legs of Eq. (deltaG3)                  */
+    int32_t precision;        /* NPB_FP64 or NPB_FP32_SWEEP                            */
+    int32_t eps_mode;         /* NPB_EPS_HARMONIC (default) or NPB_EPS_MIDPOINT        */
+} npb_opts;
+
+typedef struct {
+    double dG_kcal_mol;   /* solvation energy, Eq. (deltaG3)                          */
+    double wall_ms;       /* submit -> completion                                     */
+    double queue_ms;      /* submit -> admission                                      */
+    int64_t point_steps;  /* interior nodes x steps, summed over legs                 */
+    int32_t status;       /* NPB_OK or a negative code                                */
+    int32_t n[3];         /* grid of the request                                      */
+} npb_result;
+
+/* ---- context ------------------------------------------------------------------------ */
+/* Create a context on CUDA device `device` whose solves may hold at most
+ * hbm_budget_bytes of device memory (0: 90% of the free memory).  *out owns it. */
+int npb_ctx_create(int device, size_t hbm_budget_bytes, npb_ctx **out);
+void npb_ctx_destroy(npb_ctx *ctx);
+/* Launch on `stream` (a cudaStream_t) from now on; NULL returns to the context's own
+ * non-blocking stream.  Whole solves are replayed as CUDA graphs captured on this stream. */
+int npb_ctx_set_stream(npb_ctx *ctx, void *stream);
+/* 1: bracket every kernel launch with CUDA events and keep per-kernel totals. */
+int npb_ctx_profile(npb_ctx *ctx, int32_t enable);
+/* Per-kernel totals since profiling was enabled: for kernel class i < max_kernels,
+ * names[i] (static strings), launches[i] and total device ms[i].  Returns the number
+ * of classes written.  Synchronises the stream. */
+int npb_ctx_kernel_stats(npb_ctx *ctx, int32_t max_kernels, const char **names,
+                         int64_t *launches, double *ms);
+/* Bytes of device memory the context's grids hold right now. */
+int npb_ctx_memory(npb_ctx *ctx, size_t *in_use, size_t *budget);
+
+/* ---- one molecule --------------------------------------------------------------------- */
+/* Copy the problem to the device and run the set-up kernels on the context stream:
+ * the vdW-union node mask (Sec. 3.1), the trilinear charges Q grouped by x-line
+ * (Sec. 3.1, Eq. RhoEq), and the Dirichlet face data for solvent (Eq. BoundaryCond)
+ * and vacuum (the same formula with eps_in and kbar = 0).  NPB_ENOMEM when the
+ * grid would push the context over its budget. */
+int npb_grid_create(npb_ctx *ctx, const npb_problem *problem, npb_grid **out);
+void npb_grid_destroy(npb_grid *grid);
+/* Re-run every set-up kernel (mask, charge list, face data in use) from the atoms the grid
+ * already holds on the device; enqueued on the context stream, no host copy, no allocation.
+ * The results are identical to those of npb_grid_create. */
+int npb_grid_refresh(npb_grid *grid);
+/* Device bytes the grid needs for one RE+V solve at `precision`. */
+size_t npb_grid_footprint(const npb_problem *problem, int32_t precision);
+
+/* One pseudo-time leg from the trivial initial solution u = 0 (Sec. 2.2):
+ * tau = dt_scale * dt / alpha, n_steps / dt_scale steps.  dt_scale is 1 or 0.5.
+ * The result stays on the device as leg (medium, dt_scale) for npb_potential(). */
+int npb_lod_solve(npb_grid *grid, const npb_opts *opts, int32_t medium, double dt_scale);
+
+/* The RE+V solvation energy in kcal/mol: the solvent and vacuum legs at dt and (with
+ * richardson) dt/2 run batched on the device, then the FP64 charge-weighted sum
+ *   dG = 1/2 * 0.592183 * sum_p Q_p [(2 u_s^{dt/2} - u_s^{dt}) - (2 u_v^{dt/2} - u_v^{dt})]_p
+ * of Eqs. (rich) and (deltaG3).  Blocks until the value is on the host. */
+int npb_energy(npb_grid *grid, const npb_opts *opts, double *dG_kcal_mol);
+
+/* Copy leg `leg` (NPB_LEG_*) of the last solve to host_out as dense FP64 values of u
+ * (dimensionless), nz*ny*nx of them, x fastest.  n_elems must equal nx*ny*nz. */
+int npb_potential(npb_grid *grid, int32_t leg, double *host_out, size_t n_elems);
+
+/* Row-level access to single LOD stages: load the dense FP64 field u_inout (nz*ny*nx)
+ * into leg `leg`'s state (rounded to opts->precision), apply stage `op` (NPB_OP_*)
+ * with that leg's medium and tau = dt/alpha (halved for the *_HALF legs), and copy the
+ * result back.  Faces are never changed by any stage. */
+int npb_apply(npb_grid *grid, const npb_opts *opts, int32_t leg, int32_t op, double *u_inout,
+              size_t n_elems);
+
+/* Copy set-up arrays out (NPB_EXPORT_*); host_out must hold n_elems elements of the
+ * stated type and n_elems must equal nx*ny*nz. */
+int npb_grid_export(npb_grid *grid, int32_t what, void *host_out, size_t n_elems);
+
+/* ---- serving: continuous batching ---------------------------------------------------- */
+/* Queue one RE+V energy request; the library copies the problem.  A scheduler thread
+ * admits queued requests while their device footprint fits the budget, runs the legs
+ * of every admitted request in shared batched launches, and retires requests as they
+ * finish, so requests that arrive while others run join the running batch. */
+int npb_submit(npb_ctx *ctx, const npb_problem *problem, const npb_opts *opts,
+               uint64_t *ticket);
+/* Wait up to timeout_ms (0: do not wait, <0: wait forever) for `ticket`.  NPB_OK with
+ * *out filled (the ticket is then consumed), NPB_PENDING, or a negative code. */
+int npb_poll(npb_ctx *ctx, uint64_t ticket, int32_t timeout_ms, npb_result *out);
+
+/* ---- line-solver autotuning ------------------------------------------------------------ */
+/* Each line of a sweep is solved by SEG threads holding L consecutive rows each (a
+ * Thomas / parallel-cyclic-reduction hybrid), TX lines per thread block.  npb_autotune
+ * times every instantiated (TX, SEG, L) that covers the grid's lines, on all four legs of
+ * `grid` at opts->precision, `reps` launches each, and keeps the fastest per (precision,
+ * direction, line length) in the context.  report (may be NULL) receives a JSON list of
+ * the timings, truncated to report_len bytes.  The legs' states are overwritten. */
+int npb_autotune(npb_grid *grid, const npb_opts *opts, int32_t reps, char *report, size_t report_len);
+/* Pin / read the shape used for lines of n nodes along dir (0 = x, 1 = y, 2 = z). */
+int npb_tune_set(npb_ctx *ctx, int32_t precision, int32_t dir, int32_t n, int32_t tx, int32_t seg,
+                 int32_t len);
+int npb_tune_get(npb_ctx *ctx, int32_t precision, int32_t dir, int32_t n, int32_t *tx, int32_t *seg,
+                 int32_t *len);
+
+/* ---- errors --------------------------------------------------------------------------- */
+const char *npb_last_error(void);
+const char *npb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NPB_H */

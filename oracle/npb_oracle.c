@@ -114,6 +114,7 @@ void or_boundary(int nx, int ny, int nz, double h, const double *origin, int n_a
                  const double *xyz, const double *q, double eps, double kbar, double C,
                  double *u) {
     const double sq = sqrt(eps);
+#pragma omp parallel for collapse(2) schedule(dynamic, 4) num_threads(g_threads)
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {

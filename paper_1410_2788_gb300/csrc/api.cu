@@ -1,0 +1,827 @@
+// api.cu -- host runtime behind include/npb.h: contexts, grids, leg scheduling, CUDA-graph
+// replay of whole RE+V solves, per-kernel profiling, and the serving scheduler.
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/npb.h"
+#include "npb_internal.cuh"
+#include "runtime.h"
+#include "setup_kernels.cuh"
+
+using namespace npb;
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string t_err;
+
+int npb::fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_err = buf;
+    return code;
+}
+
+#define CU(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(NPB_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                              \
+    } while (0)
+
+extern "C" const char *npb_last_error(void) { return t_err.c_str(); }
+extern "C" const char *npb_version(void) { return "npb-lod-gb300 1.0 (sm_103a)"; }
+
+namespace npb {
+cudaError_t launch_sweep_f32(int dir, const LegDev *legs, int n_legs, int nx, int ny, int nz, int flags,
+                             SweepShape s, cudaStream_t st);
+cudaError_t launch_sweep_f64(int dir, const LegDev *legs, int n_legs, int nx, int ny, int nz, int flags,
+                             SweepShape s, cudaStream_t st);
+cudaError_t prepare_sweep_f32();
+cudaError_t prepare_sweep_f64();
+cudaError_t launch_energy(int prec, const void *s_tau, const void *s_half, const void *v_tau,
+                          const void *v_half, const int64_t *off, const double *qt, const int32_t *n_ent,
+                          int richardson, double *out, cudaStream_t st);
+
+// Shapes the line solver is instantiated for (kept in sync with NPB_SWEEP_SHAPES).
+static const SweepShape kShapes[] = {{16, 2, 17}, {16, 4, 9},   {16, 4, 17}, {16, 8, 9},
+                                     {16, 8, 13}, {16, 8, 17},  {16, 16, 9}, {16, 16, 11},
+                                     {16, 16, 17}, {16, 32, 9}, {32, 8, 17}, {32, 16, 9}};
+
+int sweep_shapes(int, SweepShape *out, int max) {
+    int n = 0;
+    for (const auto &s : kShapes)
+        if (n < max) out[n++] = s;
+    return n;
+}
+
+bool sweep_shape_available(int, SweepShape s) {
+    for (const auto &k : kShapes)
+        if (k.tx == s.tx && k.seg == s.seg && k.len == s.len) return true;
+    return false;
+}
+
+// Smallest SEG*L >= n among the TX = 16 shapes; ties go to the longer segment.
+SweepShape default_sweep_shape(int, int, int n) {
+    SweepShape best{0, 0, 0};
+    for (const auto &s : kShapes) {
+        if (s.tx != 16 || s.seg * s.len < n) continue;
+        if (best.tx == 0 || s.seg * s.len < best.seg * best.len ||
+            (s.seg * s.len == best.seg * best.len && s.len > best.len))
+            best = s;
+    }
+    return best;
+}
+
+cudaError_t launch_sweep(int prec, int dir, const LegDev *legs, int n_legs, int nx, int ny, int nz, int flags,
+                         SweepShape s, cudaStream_t st) {
+    if (prec == NPB_FP64) return launch_sweep_f64(dir, legs, n_legs, nx, ny, nz, flags, s, st);
+    return launch_sweep_f32(dir, legs, n_legs, nx, ny, nz, flags, s, st);
+}
+
+const char *kKernelNames[K_COUNT] = {"sweep_x", "sweep_y", "sweep_z", "nonlinear", "source", "init_leg",
+                                     "energy", "setup_mask", "setup_charges", "setup_boundary", "pad"};
+}  // namespace npb
+
+// ------------------------------------------------------------------ context
+Profiler::~Profiler() {
+    for (auto &p : pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+}
+
+int Profiler::begin(cudaStream_t st, cudaEvent_t *a) {
+    if (!enabled) return 0;
+    CU(cudaEventCreate(a));
+    CU(cudaEventRecord(*a, st));
+    return 0;
+}
+
+int Profiler::end(cudaStream_t st, cudaEvent_t a, int kind) {
+    if (!enabled) return 0;
+    cudaEvent_t b;
+    CU(cudaEventCreate(&b));
+    CU(cudaEventRecord(b, st));
+    std::lock_guard<std::mutex> lk(mu);
+    pending.push_back({a, b, kind});
+    return 0;
+}
+
+int Profiler::collect() {
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto &p : pending) {
+        CU(cudaEventSynchronize(p.b));
+        float ms = 0.f;
+        CU(cudaEventElapsedTime(&ms, p.a, p.b));
+        launches[p.kind] += 1;
+        total_ms[p.kind] += ms;
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    pending.clear();
+    return 0;
+}
+
+int Ctx::alloc(void **p, size_t bytes) {
+    if (bytes == 0) {
+        *p = nullptr;
+        return 0;
+    }
+    size_t cur = in_use.load();
+    if (cur + bytes > budget)
+        return fail(NPB_ENOMEM, "HBM budget exceeded: %zu in use + %zu requested > %zu budget", cur, bytes,
+                    budget);
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(NPB_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    in_use += bytes;
+    return 0;
+}
+
+void Ctx::release(void *p, size_t bytes) {
+    if (!p) return;
+    cudaFree(p);
+    in_use -= bytes;
+}
+
+extern "C" int npb_ctx_create(int device, size_t budget, npb_ctx **out) {
+    if (!out) return fail(NPB_EINVAL, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    CU(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(NPB_EINVAL, "device %d out of range (%d devices)", device, ndev);
+    CU(cudaSetDevice(device));
+    cudaDeviceProp prop;
+    CU(cudaGetDeviceProperties(&prop, device));
+    auto ctx = std::make_unique<npb_ctx>();
+    ctx->device = device;
+    ctx->sm_count = prop.multiProcessorCount;
+    size_t free_b = 0, total_b = 0;
+    CU(cudaMemGetInfo(&free_b, &total_b));
+    ctx->budget = budget ? budget : (size_t)(0.9 * (double)free_b);
+    CU(cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking));
+    ctx->stream = ctx->own_stream;
+    CU(prepare_sweep_f32());
+    CU(prepare_sweep_f64());
+    *out = ctx.release();
+    return NPB_OK;
+}
+
+extern "C" void npb_ctx_destroy(npb_ctx *ctx) {
+    if (!ctx) return;
+    serve_shutdown(ctx);
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+    delete ctx;
+}
+
+extern "C" int npb_ctx_set_stream(npb_ctx *ctx, void *stream) {
+    if (!ctx) return fail(NPB_EINVAL, "ctx is NULL");
+    ctx->stream = stream ? (cudaStream_t)stream : ctx->own_stream;
+    return NPB_OK;
+}
+
+extern "C" int npb_ctx_profile(npb_ctx *ctx, int32_t enable) {
+    if (!ctx) return fail(NPB_EINVAL, "ctx is NULL");
+    int rc = ctx->prof.collect();
+    if (rc) return rc;
+    ctx->prof.enabled = enable != 0;
+    if (enable) {
+        for (int i = 0; i < K_COUNT; ++i) {
+            ctx->prof.launches[i] = 0;
+            ctx->prof.total_ms[i] = 0.0;
+        }
+    }
+    return NPB_OK;
+}
+
+extern "C" int npb_ctx_kernel_stats(npb_ctx *ctx, int32_t max_kernels, const char **names, int64_t *launches,
+                                    double *ms) {
+    if (!ctx) return fail(NPB_EINVAL, "ctx is NULL");
+    int rc = ctx->prof.collect();
+    if (rc) return rc;
+    int n = 0;
+    for (int i = 0; i < K_COUNT && n < max_kernels; ++i, ++n) {
+        if (names) names[n] = kKernelNames[i];
+        if (launches) launches[n] = ctx->prof.launches[i];
+        if (ms) ms[n] = ctx->prof.total_ms[i];
+    }
+    return n;
+}
+
+extern "C" int npb_ctx_memory(npb_ctx *ctx, size_t *in_use, size_t *budget) {
+    if (!ctx) return fail(NPB_EINVAL, "ctx is NULL");
+    if (in_use) *in_use = ctx->in_use.load();
+    if (budget) *budget = ctx->budget;
+    return NPB_OK;
+}
+
+// ------------------------------------------------------------------ grid set-up
+static int validate(const npb_problem *p, double origin[3]) {
+    if (!p) return fail(NPB_EINVAL, "problem is NULL");
+    for (int d = 0; d < 3; ++d)
+        if (p->n[d] < 3 || p->n[d] > kMaxLine)
+            return fail(NPB_EINVAL, "n[%d] = %d outside [3, %d]", d, p->n[d], kMaxLine);
+    if (!(p->h > 0)) return fail(NPB_EINVAL, "h must be > 0");
+    if (!(p->eps_in > 0) || !(p->eps_out > 0)) return fail(NPB_EINVAL, "eps_in and eps_out must be > 0");
+    if (!(p->kappa2 >= 0)) return fail(NPB_EINVAL, "kappa2 must be >= 0");
+    if (p->n_atoms < 0) return fail(NPB_EINVAL, "n_atoms < 0");
+    if (p->n_atoms > 0 && (!p->xyz || !p->q || !p->radius)) return fail(NPB_EINVAL, "atom arrays are NULL");
+    // origin: NaN means centre the atoms' bounding box
+    for (int d = 0; d < 3; ++d) {
+        origin[d] = p->origin[d];
+        if (std::isnan(origin[d])) {
+            double lo = 0, hi = 0;
+            for (int a = 0; a < p->n_atoms; ++a) {
+                const double x = p->xyz[3 * a + d];
+                if (a == 0 || x < lo) lo = x;
+                if (a == 0 || x > hi) hi = x;
+            }
+            origin[d] = 0.5 * (lo + hi) - 0.5 * (p->n[d] - 1) * p->h;
+        }
+    }
+    for (int a = 0; a < p->n_atoms; ++a) {
+        if (!(p->radius[a] > 0)) return fail(NPB_EINVAL, "atom %d: radius must be > 0", a);
+        for (int d = 0; d < 3; ++d) {
+            const double s = (p->xyz[3 * a + d] - origin[d]) / p->h;
+            if (!std::isfinite(s)) return fail(NPB_EINVAL, "atom %d: non-finite position", a);
+            const double i0 = std::floor(s);
+            if (i0 < 1 || i0 + 1 > p->n[d] - 2)
+                return fail(NPB_EINVAL, "atom %d: charge stencil leaves the interior along axis %d", a, d);
+        }
+    }
+    return 0;
+}
+
+static size_t state_bytes(const int n[3], int prec) {
+    const size_t pitch = (size_t)(n[0] + 31) / 32 * 32;
+    return pitch * n[1] * n[2] * (prec == NPB_FP64 ? 8 : 4);
+}
+
+extern "C" size_t npb_grid_footprint(const npb_problem *p, int32_t precision) {
+    if (!p) return 0;
+    const size_t pitch = (size_t)(p->n[0] + 31) / 32 * 32;
+    const size_t lines = (size_t)p->n[1] * p->n[2];
+    const size_t na = p->n_atoms > 0 ? p->n_atoms : 0;
+    size_t b = 0;
+    b += 4 * state_bytes(p->n, precision);                       // four leg states
+    b += (pitch / 32) * lines * 4;                                // node mask
+    b += 2 * lines * 4 + 8 * na * (4 + 8 + 8);                    // charge list
+    b += 4 * (size_t)face_count(p->n[0], p->n[1], p->n[2]) * 8;  // face data, 2 media x 2 kinds
+    b += na * 5 * 8 + 4096;                                       // atoms, result slot
+    return b;
+}
+
+template <typename T>
+static int galloc(npb_grid *g, T **p, size_t count) {
+    void *v = nullptr;
+    int rc = g->ctx->alloc(&v, count * sizeof(T));
+    if (rc) return rc;
+    g->allocs.push_back({v, count * sizeof(T)});
+    *p = static_cast<T *>(v);
+    return 0;
+}
+
+void npb::grid_free(npb_grid *g) {
+    if (!g) return;
+    cudaSetDevice(g->ctx->device);
+    cudaStreamSynchronize(g->ctx->stream);
+    for (auto &c : g->graphs) {
+        if (c.exec) cudaGraphExecDestroy(c.exec);
+    }
+    for (auto &a : g->allocs) g->ctx->release(a.p, a.bytes);
+    if (g->h_result) cudaFreeHost(g->h_result);
+    delete g;
+}
+
+int npb::grid_build(npb_ctx *ctx, const npb_problem *p, cudaStream_t st, npb_grid **out) {
+    *out = nullptr;
+    double origin[3];
+    int rc = validate(p, origin);
+    if (rc) return rc;
+    CU(cudaSetDevice(ctx->device));
+    auto g = new npb_grid();
+    g->ctx = ctx;
+    g->geo.nx = p->n[0];
+    g->geo.ny = p->n[1];
+    g->geo.nz = p->n[2];
+    g->geo.pitch = (p->n[0] + 31) / 32 * 32;
+    g->geo.h = p->h;
+    g->geo.ox = origin[0];
+    g->geo.oy = origin[1];
+    g->geo.oz = origin[2];
+    g->eps_in = p->eps_in;
+    g->eps_out = p->eps_out;
+    g->kappa2 = p->kappa2;
+    g->n_atoms = p->n_atoms;
+    const int na = p->n_atoms;
+    const int n_lines = g->geo.ny * g->geo.nz;
+    const size_t words = (size_t)(g->geo.pitch / 32) * n_lines;
+    auto guard = [&](int r) {
+        if (r) grid_free(g);
+        return r;
+    };
+    if ((rc = galloc(g, &g->d_xyz, std::max(1, 3 * na)))) return guard(rc);
+    if ((rc = galloc(g, &g->d_q, std::max(1, na)))) return guard(rc);
+    if ((rc = galloc(g, &g->d_rad, std::max(1, na)))) return guard(rc);
+    if ((rc = galloc(g, &g->d_mask, words))) return guard(rc);
+    if ((rc = galloc(g, &g->d_line_begin, n_lines))) return guard(rc);
+    if ((rc = galloc(g, &g->d_line_count, n_lines))) return guard(rc);
+    const int n_raw = std::max(1, 8 * na);
+    if ((rc = galloc(g, &g->d_ent_x, n_raw))) return guard(rc);
+    if ((rc = galloc(g, &g->d_ent_qt, n_raw))) return guard(rc);
+    if ((rc = galloc(g, &g->d_ent_off, n_raw))) return guard(rc);
+    if ((rc = galloc(g, &g->d_result, 8))) return guard(rc);
+    if (cudaMallocHost(&g->h_result, 8 * sizeof(double)) != cudaSuccess) {
+        g->h_result = nullptr;
+        return guard(fail(NPB_ENOMEM, "cudaMallocHost failed"));
+    }
+    if (na > 0) {
+        CU(cudaMemcpyAsync(g->d_xyz, p->xyz, sizeof(double) * 3 * na, cudaMemcpyHostToDevice, st));
+        CU(cudaMemcpyAsync(g->d_q, p->q, sizeof(double) * na, cudaMemcpyHostToDevice, st));
+        CU(cudaMemcpyAsync(g->d_rad, p->radius, sizeof(double) * na, cudaMemcpyHostToDevice, st));
+    }
+    (void)words;
+    // charge list, with scratch released at the end of set-up
+    // charge-list scratch stays with the grid so that set-up can be re-run without allocating
+    const size_t ints = 3 * (size_t)n_lines + 4;
+    g->scratch_bytes = ints * sizeof(int32_t) + 2 * sizeof(RawEntry) * n_raw + 64;
+    if ((rc = ctx->alloc(&g->d_scratch, g->scratch_bytes))) return guard(rc);
+    g->allocs.push_back({g->d_scratch, g->scratch_bytes});
+    ChargeScratch &sc = g->sc;
+    sc.count = (int32_t *)g->d_scratch;
+    sc.fill = sc.count + n_lines;
+    sc.raw_begin = sc.fill + n_lines;
+    sc.total = sc.raw_begin + n_lines;
+    uintptr_t rp = ((uintptr_t)(sc.total + 4) + 15) & ~(uintptr_t)15;
+    sc.raw = (RawEntry *)rp;
+    sc.bucket = sc.raw + n_raw;
+    if ((rc = grid_setup(g, st))) return guard(rc);
+    int32_t total = 0;
+    CU(cudaMemcpyAsync(&total, sc.total, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    g->n_ent = total;
+    *out = g;
+    return 0;
+}
+
+// Set-up kernels from the grid's resident atoms: node mask (and half-point masks when
+// they exist), charge list, and every face array already in use.  No allocation, no sync.
+int npb::grid_setup(npb_grid *g, cudaStream_t st) {
+    Profiler &pr = g->ctx->prof;
+    const int na = g->n_atoms;
+    const size_t words = (size_t)(g->geo.pitch / 32) * g->geo.ny * g->geo.nz;
+    int rc;
+    cudaEvent_t ev{};
+    CU(cudaMemsetAsync(g->d_mask, 0, words * 4, st));
+    for (int d = 0; d < 3; ++d)
+        if (g->d_half[d]) CU(cudaMemsetAsync(g->d_half[d], 0, words * 4, st));
+    if ((rc = pr.begin(st, &ev))) return rc;
+    CU(setup_mask(g->geo, g->d_xyz, g->d_rad, na, g->d_mask, g->d_half[0], g->d_half[1], g->d_half[2], st));
+    if ((rc = pr.end(st, ev, K_SETUP_MASK))) return rc;
+    if ((rc = pr.begin(st, &ev))) return rc;
+    CU(setup_charges(g->geo, g->d_xyz, g->d_q, na, g->sc, g->d_line_begin, g->d_line_count, g->d_ent_x,
+                     g->d_ent_qt, g->d_ent_off, st));
+    if ((rc = pr.end(st, ev, K_SETUP_CHARGES))) return rc;
+    for (int m = 0; m < 2; ++m)
+        for (int k = 0; k < 2; ++k) {
+            if (!g->d_bc[m][k]) continue;
+            const double eps = m == NPB_SOLVENT ? g->eps_out : g->eps_in;
+            const double kbar = m == NPB_SOLVENT ? std::sqrt(g->kappa2) : 0.0;
+            if ((rc = pr.begin(st, &ev))) return rc;
+            CU(setup_boundary(g->geo, g->d_xyz, g->d_q, na, eps, kbar, k == 1, g->d_bc[m][k], st));
+            if ((rc = pr.end(st, ev, K_SETUP_BOUNDARY))) return rc;
+        }
+    return 0;
+}
+
+extern "C" int npb_grid_refresh(npb_grid *g) {
+    if (!g) return fail(NPB_EINVAL, "grid is NULL");
+    CU(cudaSetDevice(g->ctx->device));
+    return grid_setup(g, g->ctx->stream);
+}
+
+extern "C" int npb_grid_create(npb_ctx *ctx, const npb_problem *p, npb_grid **out) {
+    if (!ctx || !out) return fail(NPB_EINVAL, "ctx/out is NULL");
+    return grid_build(ctx, p, ctx->stream, out);
+}
+
+extern "C" void npb_grid_destroy(npb_grid *g) { grid_free(g); }
+
+// Face data of a medium, computed on first use with FP64 (parity path) or FP32 pair
+// terms (mixed path), then cached.
+int npb::grid_boundary(npb_grid *g, int medium, int prec, cudaStream_t st, const double **out) {
+    const int kind = prec == NPB_FP64 ? 0 : 1;
+    double *&bc = g->d_bc[medium][kind];
+    if (!bc) {
+        const int64_t nf = face_count(g->geo.nx, g->geo.ny, g->geo.nz);
+        int rc = galloc(g, &bc, (size_t)nf);
+        if (rc) return rc;
+        const double eps = medium == NPB_SOLVENT ? g->eps_out : g->eps_in;
+        const double kbar = medium == NPB_SOLVENT ? std::sqrt(g->kappa2) : 0.0;
+        cudaEvent_t ev{};
+        if ((rc = g->ctx->prof.begin(st, &ev))) return rc;
+        CU(setup_boundary(g->geo, g->d_xyz, g->d_q, g->n_atoms, eps, kbar, kind == 1, bc, st));
+        if ((rc = g->ctx->prof.end(st, ev, K_SETUP_BOUNDARY))) return rc;
+    }
+    *out = bc;
+    return 0;
+}
+
+int npb::grid_half_masks(npb_grid *g, cudaStream_t st) {
+    if (g->d_half[0]) return 0;
+    const size_t words = (size_t)(g->geo.pitch / 32) * g->geo.ny * g->geo.nz;
+    for (int d = 0; d < 3; ++d) {
+        int rc = galloc(g, &g->d_half[d], words);
+        if (rc) return rc;
+        CU(cudaMemsetAsync(g->d_half[d], 0, words * 4, st));
+    }
+    // the node mask is rebuilt alongside (atomicOr keeps it identical)
+    CU(setup_mask(g->geo, g->d_xyz, g->d_rad, g->n_atoms, g->d_mask, g->d_half[0], g->d_half[1], g->d_half[2],
+                  st));
+    return 0;
+}
+
+// ------------------------------------------------------------------ legs
+// Device leg table order: [s_half, v_half, s_tau, v_tau], so that the legs still running
+// after step n (the dt/2 legs) form a prefix.
+const int npb::kLegSlot[4] = {2, 0, 3, 1};  // NPB_LEG_* -> slot
+
+int npb::grid_states(npb_grid *g, int prec, cudaStream_t st) {
+    if (g->d_u[prec][0]) return 0;
+    int n[3] = {g->geo.nx, g->geo.ny, g->geo.nz};
+    const size_t bytes = state_bytes(n, prec);
+    for (int s = 0; s < 4; ++s) {
+        unsigned char *p = nullptr;
+        int rc = galloc(g, &p, bytes);
+        if (rc) return rc;
+        CU(cudaMemsetAsync(p, 0, bytes, st));
+        g->d_u[prec][s] = p;
+    }
+    int rc = galloc(g, &g->d_legs[prec], 4);
+    if (rc) return rc;
+    g->legs_key[prec] = "";
+    return 0;
+}
+
+LegDev npb::make_leg(const npb_grid *g, int leg, const npb_opts *o) {
+    LegDev L{};
+    const int prec = o->precision;
+    const bool solvent = leg == NPB_LEG_SOLVENT_TAU || leg == NPB_LEG_SOLVENT_HALF;
+    const bool half = leg == NPB_LEG_SOLVENT_HALF || leg == NPB_LEG_VACUUM_HALF;
+    const double tau = (half ? 0.5 : 1.0) * o->dt / o->alpha;
+    const double h = g->geo.h;
+    const double r = tau / (h * h);
+    L.u = g->d_u[prec][kLegSlot[leg]];
+    L.nx = g->geo.nx;
+    L.ny = g->geo.ny;
+    L.nz = g->geo.nz;
+    L.pitch = g->geo.pitch;
+    L.line_begin = g->d_line_begin;
+    L.line_count = g->d_line_count;
+    L.ent_x = g->d_ent_x;
+    L.ent_qt = g->d_ent_qt;
+    L.src = tau * 4.0 * kPi * kBjerrum / (h * h * h);
+    L.eps_mode = o->eps_mode == NPB_EPS_MIDPOINT ? 1 : 0;
+    if (solvent) {
+        const double ei = g->eps_in, eo = g->eps_out;
+        L.mask = g->d_mask;
+        L.rE[0] = r * eo;
+        L.rE[1] = r * (2.0 * ei * eo / (ei + eo));
+        L.rE[2] = r * ei;
+        for (int d = 0; d < 3; ++d) L.half[d] = L.eps_mode ? g->d_half[d] : nullptr;
+        L.nl_on = g->kappa2 > 0 ? 1 : 0;
+        L.nl_q = std::exp(-g->kappa2 * tau);
+        L.nl_omq = -std::expm1(-g->kappa2 * tau);
+    } else {
+        L.mask = nullptr;
+        L.rE[0] = L.rE[1] = L.rE[2] = r * g->eps_in;
+        for (int d = 0; d < 3; ++d) L.half[d] = nullptr;
+        L.nl_on = 0;
+        L.nl_q = 1.0;
+        L.nl_omq = 0.0;
+    }
+    return L;
+}
+
+static int check_opts(const npb_opts *o) {
+    if (!o) return fail(NPB_EINVAL, "opts is NULL");
+    if (!(o->dt > 0) || !(o->alpha > 0)) return fail(NPB_EINVAL, "dt and alpha must be > 0");
+    if (o->n_steps < 0) return fail(NPB_EINVAL, "n_steps < 0");
+    if (o->scheme != NPB_LODIE1 && o->scheme != NPB_LODIE2) return fail(NPB_EINVAL, "unknown scheme %d", o->scheme);
+    if (o->precision != NPB_FP64 && o->precision != NPB_FP32_SWEEP)
+        return fail(NPB_EINVAL, "unknown precision %d", o->precision);
+    if (o->eps_mode != NPB_EPS_HARMONIC && o->eps_mode != NPB_EPS_MIDPOINT)
+        return fail(NPB_EINVAL, "unknown eps_mode %d", o->eps_mode);
+    return 0;
+}
+
+// Upload the leg table (as the solve's opts say) once per change.
+int npb::grid_prepare(npb_grid *g, const npb_opts *o, cudaStream_t st) {
+    int rc = grid_states(g, o->precision, st);
+    if (rc) return rc;
+    if (o->eps_mode == NPB_EPS_MIDPOINT && (rc = grid_half_masks(g, st))) return rc;
+    const int prec = o->precision;
+    g->u_prec = prec;
+    char key[256];
+    snprintf(key, sizeof key, "%.17g/%.17g/%d", o->dt, o->alpha, o->eps_mode);
+    if (g->legs_key[prec] == key) return 0;
+    for (int leg = 0; leg < 4; ++leg) g->h_legs[prec][kLegSlot[leg]] = make_leg(g, leg, o);
+    CU(cudaMemcpyAsync(g->d_legs[prec], g->h_legs[prec], sizeof(LegDev) * 4, cudaMemcpyHostToDevice, st));
+    CU(cudaStreamSynchronize(st));
+    g->legs_key[prec] = key;
+    return 0;
+}
+
+SweepShape npb::shape_for(npb_ctx *ctx, int prec, int dir, int n) {
+    std::lock_guard<std::mutex> lk(ctx->tune_mu);
+    auto it = ctx->tuned.find(tune_key(prec, dir, n));
+    if (it != ctx->tuned.end()) return it->second;
+    return default_sweep_shape(prec, dir, n);
+}
+
+// One LOD step for legs [slot0, slot0 + n_legs) of the device table.
+int npb::run_step(npb_grid *g, int prec, int scheme, int slot0, int n_legs, cudaStream_t st) {
+    Profiler &pr = g->ctx->prof;
+    const LegDev *legs = g->d_legs[prec] + slot0;
+    const int nx = g->geo.nx, ny = g->geo.ny, nz = g->geo.nz;
+    const int n_dir[3] = {nx, ny, nz};
+    for (int d = 0; d < 3; ++d) {
+        int flags = 0;
+        if (d == 0) flags = scheme == NPB_LODIE2 ? FUSE_PRE_SRC : FUSE_PRE_NL;
+        if (d == 2 && scheme == NPB_LODIE2) flags = FUSE_POST_NL;
+        const SweepShape s = shape_for(g->ctx, prec, d, n_dir[d]);
+        cudaEvent_t ev{};
+        int rc = pr.begin(st, &ev);
+        if (rc) return rc;
+        CU(launch_sweep(prec, d, legs, n_legs, nx, ny, nz, flags, s, st));
+        if ((rc = pr.end(st, ev, K_SWEEP_X + d))) return rc;
+    }
+    if (scheme == NPB_LODIE1) {
+        cudaEvent_t ev{};
+        int rc = pr.begin(st, &ev);
+        if (rc) return rc;
+        CU(launch_source(prec, legs, n_legs, ny, nz, st));
+        if ((rc = pr.end(st, ev, K_SOURCE))) return rc;
+    }
+    return 0;
+}
+
+int npb::init_legs(npb_grid *g, int prec, const int *legs, int n, cudaStream_t st) {
+    for (int i = 0; i < n; ++i) {
+        const int leg = legs[i];
+        const int medium = (leg == NPB_LEG_SOLVENT_TAU || leg == NPB_LEG_SOLVENT_HALF) ? NPB_SOLVENT : NPB_VACUUM;
+        const double *bc = nullptr;
+        int rc = grid_boundary(g, medium, prec, st, &bc);
+        if (rc) return rc;
+        cudaEvent_t ev{};
+        if ((rc = g->ctx->prof.begin(st, &ev))) return rc;
+        CU(init_leg(prec, g->geo, bc, g->d_u[prec][kLegSlot[leg]], st));
+        if ((rc = g->ctx->prof.end(st, ev, K_INIT))) return rc;
+    }
+    return 0;
+}
+
+// The whole RE+V solve as a stream of launches: init, steps, energy, result read-back.
+int npb::enqueue_energy(npb_grid *g, const npb_opts *o, cudaStream_t st) {
+    const int prec = o->precision;
+    const int re = o->richardson ? 1 : 0;
+    const int n = o->n_steps;
+    const int legs_re[4] = {NPB_LEG_SOLVENT_TAU, NPB_LEG_SOLVENT_HALF, NPB_LEG_VACUUM_TAU, NPB_LEG_VACUUM_HALF};
+    const int legs_plain[2] = {NPB_LEG_SOLVENT_TAU, NPB_LEG_VACUUM_TAU};
+    int rc = init_legs(g, prec, re ? legs_re : legs_plain, re ? 4 : 2, st);
+    if (rc) return rc;
+    if (re) {
+        // steps 1..n: all four legs (slots 0..3); steps n+1..2n: the dt/2 legs (slots 0..1)
+        for (int s = 0; s < n; ++s)
+            if ((rc = run_step(g, prec, o->scheme, 0, 4, st))) return rc;
+        for (int s = 0; s < n; ++s)
+            if ((rc = run_step(g, prec, o->scheme, 0, 2, st))) return rc;
+    } else {
+        // slots 2..3 hold the dt legs
+        for (int s = 0; s < n; ++s)
+            if ((rc = run_step(g, prec, o->scheme, 2, 2, st))) return rc;
+    }
+    cudaEvent_t ev{};
+    if ((rc = g->ctx->prof.begin(st, &ev))) return rc;
+    void *const *U = g->d_u[prec];
+    CU(launch_energy(prec, U[kLegSlot[0]], U[kLegSlot[1]], U[kLegSlot[2]], U[kLegSlot[3]],
+                     g->d_ent_off, g->d_ent_qt, g->sc.total, re, g->d_result, st));
+    if ((rc = g->ctx->prof.end(st, ev, K_ENERGY))) return rc;
+    CU(cudaMemcpyAsync(g->h_result, g->d_result, sizeof(double), cudaMemcpyDeviceToHost, st));
+    return 0;
+}
+
+extern "C" int npb_energy(npb_grid *g, const npb_opts *o, double *dG) {
+    if (!g || !dG) return fail(NPB_EINVAL, "grid/dG is NULL");
+    int rc = check_opts(o);
+    if (rc) return rc;
+    if (!o->vacuum_recovery)
+        return fail(NPB_EINVAL, "vacuum_recovery = 0 needs the FFT vacuum potential, which is not provided");
+    npb_ctx *ctx = g->ctx;
+    CU(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    if ((rc = grid_prepare(g, o, st))) return rc;
+    // boundary data are computed on first use, outside any graph capture
+    const int legs[4] = {0, 1, 2, 3};
+    for (int i = 0; i < 4; ++i) {
+        const double *bc;
+        if ((rc = grid_boundary(g, legs[i] < 2 ? NPB_SOLVENT : NPB_VACUUM, o->precision, st, &bc))) return rc;
+    }
+    const bool use_graph = !ctx->prof.enabled && st != nullptr && ctx->use_graphs;
+    if (use_graph) {
+        char key[256];
+        snprintf(key, sizeof key, "%d/%d/%d/%d/%d/%s", o->precision, o->scheme, o->richardson, o->n_steps,
+                 o->eps_mode, g->legs_key[o->precision].c_str());
+        GraphCache *hit = nullptr;
+        for (auto &c : g->graphs)
+            if (c.key == key && c.stream == st) hit = &c;
+        if (!hit) {
+            cudaGraph_t graph;
+            CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            rc = enqueue_energy(g, o, st);
+            cudaError_t ec = cudaStreamEndCapture(st, &graph);
+            if (rc) {
+                if (ec == cudaSuccess) cudaGraphDestroy(graph);
+                return rc;
+            }
+            CU(ec);
+            GraphCache c;
+            c.key = key;
+            c.stream = st;
+            cudaError_t ei = cudaGraphInstantiate(&c.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            CU(ei);
+            g->graphs.push_back(c);
+            hit = &g->graphs.back();
+        }
+        CU(cudaGraphLaunch(hit->exec, st));
+    } else {
+        if ((rc = enqueue_energy(g, o, st))) return rc;
+    }
+    CU(cudaStreamSynchronize(st));
+    *dG = g->h_result[0];
+    return NPB_OK;
+}
+
+extern "C" int npb_lod_solve(npb_grid *g, const npb_opts *o, int32_t medium, double dt_scale) {
+    if (!g) return fail(NPB_EINVAL, "grid is NULL");
+    int rc = check_opts(o);
+    if (rc) return rc;
+    if (medium != NPB_SOLVENT && medium != NPB_VACUUM) return fail(NPB_EINVAL, "unknown medium %d", medium);
+    if (dt_scale != 1.0 && dt_scale != 0.5) return fail(NPB_EINVAL, "dt_scale must be 1 or 0.5");
+    CU(cudaSetDevice(g->ctx->device));
+    cudaStream_t st = g->ctx->stream;
+    if ((rc = grid_prepare(g, o, st))) return rc;
+    const int leg = medium == NPB_SOLVENT ? (dt_scale == 1.0 ? NPB_LEG_SOLVENT_TAU : NPB_LEG_SOLVENT_HALF)
+                                          : (dt_scale == 1.0 ? NPB_LEG_VACUUM_TAU : NPB_LEG_VACUUM_HALF);
+    if ((rc = init_legs(g, o->precision, &leg, 1, st))) return rc;
+    const int steps = dt_scale == 1.0 ? o->n_steps : 2 * o->n_steps;
+    for (int s = 0; s < steps; ++s)
+        if ((rc = run_step(g, o->precision, o->scheme, kLegSlot[leg], 1, st))) return rc;
+    CU(cudaStreamSynchronize(st));
+    return NPB_OK;
+}
+
+extern "C" int npb_potential(npb_grid *g, int32_t leg, double *host_out, size_t n_elems) {
+    if (!g || !host_out) return fail(NPB_EINVAL, "grid/host_out is NULL");
+    if (leg < 0 || leg > 3) return fail(NPB_EINVAL, "unknown leg %d", leg);
+    const size_t total = (size_t)g->geo.nx * g->geo.ny * g->geo.nz;
+    if (n_elems != total) return fail(NPB_EINVAL, "n_elems %zu != nx*ny*nz %zu", n_elems, total);
+    if (g->u_prec < 0 || !g->d_u[g->u_prec][0]) return fail(NPB_EINVAL, "no solve has run on this grid");
+    CU(cudaSetDevice(g->ctx->device));
+    cudaStream_t st = g->ctx->stream;
+    void *tmp = nullptr;
+    int rc = g->ctx->alloc(&tmp, total * sizeof(double));
+    if (rc) return rc;
+    cudaError_t e = unpad_state(g->u_prec, g->geo, g->d_u[g->u_prec][kLegSlot[leg]], (double *)tmp, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, tmp, total * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    g->ctx->release(tmp, total * sizeof(double));
+    if (e != cudaSuccess) return fail(NPB_ECUDA, "potential read-back failed: %s", cudaGetErrorString(e));
+    return NPB_OK;
+}
+
+extern "C" int npb_apply(npb_grid *g, const npb_opts *o, int32_t leg, int32_t op, double *u_inout,
+                         size_t n_elems) {
+    if (!g || !u_inout) return fail(NPB_EINVAL, "grid/u_inout is NULL");
+    int rc = check_opts(o);
+    if (rc) return rc;
+    if (leg < 0 || leg > 3) return fail(NPB_EINVAL, "unknown leg %d", leg);
+    if (op < NPB_OP_SOURCE || op > NPB_OP_STEP) return fail(NPB_EINVAL, "unknown op %d", op);
+    const size_t total = (size_t)g->geo.nx * g->geo.ny * g->geo.nz;
+    if (n_elems != total) return fail(NPB_EINVAL, "n_elems %zu != nx*ny*nz %zu", n_elems, total);
+    CU(cudaSetDevice(g->ctx->device));
+    cudaStream_t st = g->ctx->stream;
+    if ((rc = grid_prepare(g, o, st))) return rc;
+    void *tmp = nullptr;
+    if ((rc = g->ctx->alloc(&tmp, total * sizeof(double)))) return rc;
+    const int slot = kLegSlot[leg];
+    const int prec = o->precision;
+    void *u = g->d_u[prec][slot];
+    const LegDev *legs = g->d_legs[prec] + slot;
+    const int nx = g->geo.nx, ny = g->geo.ny, nz = g->geo.nz;
+    cudaError_t e = cudaMemcpyAsync(tmp, u_inout, total * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(u, 0, state_bytes(&g->geo.nx, prec), st);
+    if (e == cudaSuccess) e = pad_state(prec, g->geo, (const double *)tmp, u, st);
+    if (e == cudaSuccess) {
+        const int n_dir[3] = {nx, ny, nz};
+        switch (op) {
+        case NPB_OP_SOURCE: e = launch_source(prec, legs, 1, ny, nz, st); break;
+        case NPB_OP_NONLINEAR: e = launch_nonlinear(prec, legs, 1, nx, ny, nz, st); break;
+        case NPB_OP_SWEEP_X:
+        case NPB_OP_SWEEP_Y:
+        case NPB_OP_SWEEP_Z: {
+            const int d = op - NPB_OP_SWEEP_X;
+            e = launch_sweep(prec, d, legs, 1, nx, ny, nz, 0, shape_for(g->ctx, prec, d, n_dir[d]), st);
+            break;
+        }
+        case NPB_OP_STEP: {
+            int r2 = run_step(g, prec, o->scheme, slot, 1, st);
+            if (r2) {
+                cudaStreamSynchronize(st);
+                g->ctx->release(tmp, total * sizeof(double));
+                return r2;
+            }
+            break;
+        }
+        }
+    }
+    if (e == cudaSuccess) e = unpad_state(prec, g->geo, u, (double *)tmp, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(u_inout, tmp, total * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    g->ctx->release(tmp, total * sizeof(double));
+    if (e != cudaSuccess) return fail(NPB_ECUDA, "npb_apply failed: %s", cudaGetErrorString(e));
+    return NPB_OK;
+}
+
+extern "C" int npb_grid_export(npb_grid *g, int32_t what, void *host_out, size_t n_elems) {
+    if (!g || !host_out) return fail(NPB_EINVAL, "grid/host_out is NULL");
+    const size_t total = (size_t)g->geo.nx * g->geo.ny * g->geo.nz;
+    if (n_elems != total) return fail(NPB_EINVAL, "n_elems %zu != nx*ny*nz %zu", n_elems, total);
+    CU(cudaSetDevice(g->ctx->device));
+    cudaStream_t st = g->ctx->stream;
+    void *tmp = nullptr;
+    int rc = g->ctx->alloc(&tmp, total * sizeof(double));
+    if (rc) return rc;
+    cudaError_t e = cudaSuccess;
+    size_t out_bytes = total * sizeof(double);
+    switch (what) {
+    case NPB_EXPORT_MASK:
+        e = mask_dense(g->geo, g->d_mask, (uint8_t *)tmp, st);
+        out_bytes = total;
+        break;
+    case NPB_EXPORT_QTILDE:
+        e = cudaMemsetAsync(tmp, 0, total * sizeof(double), st);
+        if (e == cudaSuccess)
+            e = qt_dense(g->geo, g->d_line_begin, g->d_line_count, g->d_ent_x, g->d_ent_qt, (double *)tmp, st);
+        break;
+    case NPB_EXPORT_U0_SOLVENT:
+    case NPB_EXPORT_U0_VACUUM: {
+        const double *bc = nullptr;
+        rc = grid_boundary(g, what == NPB_EXPORT_U0_SOLVENT ? NPB_SOLVENT : NPB_VACUUM, NPB_FP64, st, &bc);
+        if (rc) {
+            g->ctx->release(tmp, total * sizeof(double));
+            return rc;
+        }
+        void *pad = nullptr;
+        int n3[3] = {g->geo.nx, g->geo.ny, g->geo.nz};
+        const size_t pb = state_bytes(n3, NPB_FP64);
+        if ((rc = g->ctx->alloc(&pad, pb))) {
+            g->ctx->release(tmp, total * sizeof(double));
+            return rc;
+        }
+        e = init_leg(NPB_FP64, g->geo, bc, pad, st);
+        if (e == cudaSuccess) e = unpad_state(NPB_FP64, g->geo, pad, (double *)tmp, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        g->ctx->release(pad, pb);
+        break;
+    }
+    default:
+        g->ctx->release(tmp, total * sizeof(double));
+        return fail(NPB_EINVAL, "unknown export %d", what);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, tmp, out_bytes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    g->ctx->release(tmp, total * sizeof(double));
+    if (e != cudaSuccess) return fail(NPB_ECUDA, "export failed: %s", cudaGetErrorString(e));
+    return NPB_OK;
+}

@@ -1,0 +1,70 @@
+// npb_internal.cuh -- device-side types shared by the GB300 LOD-NPB kernels.
+//
+// Data layout in HBM (one grid, one leg):
+//   u     : T[nz][ny][pitch], x fastest; pitch = nx rounded up to 32 elements, so
+//           every x-row starts on a 128-byte boundary.  Faces (an index 0 or n-1)
+//           hold the Dirichlet data and are never written by a sweep; padding
+//           columns x >= nx are zero.
+//   mask  : uint32[nz][ny][pitch/32]; bit x of row (y, z) is 1 on/inside the
+//           molecule (Omega_m).  Vacuum legs pass no mask (every node "inside").
+//   half  : for NPB_EPS_MIDPOINT, one such bit array per direction d, whose bit at
+//           node p says that the half point p + e_d/2 is inside.
+//   charges: entries grouped by x-line (z*ny + y): line_begin/line_count index
+//           ent_x (node x) and ent_qt (trilinear charge, e_c), and ent_off (element
+//           offset of the node in u) for gathers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace npb {
+
+constexpr double kCoulomb = 332.0637;            // kcal A / (mol e^2)
+constexpr double kKT = 0.592183;                 // kcal/mol at 298 K (Sec. 2.1)
+constexpr double kBjerrum = kCoulomb / kKT;      // e_c^2 / (k_B T) in A
+constexpr double kPi = 3.14159265358979323846;
+
+enum Dir { DIR_X = 0, DIR_Y = 1, DIR_Z = 2 };
+
+// Everything a sweep / stage kernel needs for one leg.  Lives in device memory as an
+// array indexed by blockIdx.z, so one launch can advance several legs of equal size.
+struct LegDev {
+    void *u;
+    const uint32_t *mask;      // node bits, nullptr = all inside
+    const uint32_t *half[3];   // half-point bits (midpoint eps mode), nullptr otherwise
+    const int32_t *line_begin;
+    const int32_t *line_count;
+    const int32_t *ent_x;
+    const double *ent_qt;
+    int32_t nx, ny, nz, pitch;
+    double rE[3];              // r*eps for a half point with 0, 1, 2 inside nodes
+    double src;                // tau * 4 pi C / h^3: S adds src * qtilde
+    double nl_q;               // exp(-kbar^2 tau)
+    double nl_omq;             // 1 - nl_q, as -expm1(-kbar^2 tau)
+    int32_t nl_on;             // 1: solvent nodes get the nonlinear stage
+    int32_t eps_mode;          // 0 harmonic, 1 midpoint
+};
+
+// Stage flags for the sweep kernels.
+enum : int {
+    FUSE_PRE_SRC = 1,   // X sweep: add tau Q to the loaded line (LODIE2 stage S)
+    FUSE_PRE_NL = 2,    // X sweep: nonlinear stage on the loaded line (LODIE1 stage N)
+    FUSE_POST_NL = 4,   // Z sweep: nonlinear stage before the store (LODIE2 stage N)
+};
+
+struct SweepShape {     // one instantiated line-solver shape
+    int tx, seg, len;
+};
+
+// Launchers (defined in sweep_*.cu).  Return cudaError of the launch.
+cudaError_t launch_sweep(int prec, int dir, const LegDev *legs_dev, int n_legs, int nx, int ny,
+                         int nz, int flags, SweepShape shape, cudaStream_t st);
+bool sweep_shape_available(int prec, SweepShape shape);
+SweepShape default_sweep_shape(int prec, int dir, int n_dir);
+int sweep_shapes(int prec, SweepShape *out, int max);
+
+cudaError_t launch_nonlinear(int prec, const LegDev *legs_dev, int n_legs, int nx, int ny, int nz,
+                             cudaStream_t st);
+cudaError_t launch_source(int prec, const LegDev *legs_dev, int n_legs, int ny, int nz,
+                          cudaStream_t st);
+
+}  // namespace npb

@@ -1,0 +1,133 @@
+// runtime.h -- host-side state behind the opaque handles of include/npb.h.
+#pragma once
+#include <atomic>
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/npb.h"
+#include "npb_internal.cuh"
+#include "setup_kernels.cuh"
+
+namespace npb {
+
+constexpr int kMaxLine = 288;  // longest line the instantiated solver shapes cover
+
+enum KernelKind {
+    K_SWEEP_X = 0, K_SWEEP_Y, K_SWEEP_Z, K_NONLINEAR, K_SOURCE, K_INIT, K_ENERGY,
+    K_SETUP_MASK, K_SETUP_CHARGES, K_SETUP_BOUNDARY, K_PAD, K_COUNT
+};
+extern const char *kKernelNames[K_COUNT];
+
+int fail(int code, const char *fmt, ...);
+
+// Per-kernel CUDA-event timing (only while enabled; graphs are bypassed then).
+struct Profiler {
+    struct Pending {
+        cudaEvent_t a, b;
+        int kind;
+    };
+    bool enabled = false;
+    std::mutex mu;
+    std::vector<Pending> pending;
+    int64_t launches[K_COUNT] = {};
+    double total_ms[K_COUNT] = {};
+    ~Profiler();
+    int begin(cudaStream_t st, cudaEvent_t *a);
+    int end(cudaStream_t st, cudaEvent_t a, int kind);
+    int collect();
+};
+
+struct ServeState;  // serving scheduler (serve.cu)
+
+inline int64_t tune_key(int prec, int dir, int n) { return ((int64_t)prec << 40) | ((int64_t)dir << 32) | n; }
+
+}  // namespace npb
+
+struct npb_ctx {
+    int device = 0;
+    int sm_count = 0;
+    size_t budget = 0;
+    std::atomic<size_t> in_use{0};
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    bool use_graphs = true;
+    npb::Profiler prof;
+    std::mutex tune_mu;
+    std::map<int64_t, npb::SweepShape> tuned;  // autotuned line-solver shapes
+    npb::ServeState *serve = nullptr;
+    int alloc(void **p, size_t bytes);
+    void release(void *p, size_t bytes);
+};
+
+namespace npb {
+using Ctx = ::npb_ctx;
+
+struct GraphCache {
+    std::string key;
+    cudaStream_t stream = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+struct Alloc {
+    void *p;
+    size_t bytes;
+};
+
+}  // namespace npb
+
+struct npb_grid {
+    npb_ctx *ctx = nullptr;
+    npb::GridGeom geo{};
+    double eps_in = 1, eps_out = 80, kappa2 = 0;
+    int n_atoms = 0;
+    double *d_xyz = nullptr, *d_q = nullptr, *d_rad = nullptr;
+    uint32_t *d_mask = nullptr;
+    uint32_t *d_half[3] = {nullptr, nullptr, nullptr};
+    int32_t *d_line_begin = nullptr, *d_line_count = nullptr, *d_ent_x = nullptr;
+    double *d_ent_qt = nullptr;
+    int64_t *d_ent_off = nullptr;
+    int n_ent = 0;
+    double *d_bc[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [medium][0 fp64 | 1 fp32 pairs]
+    void *d_u[2][4] = {};              // leg states by [precision][slot]
+    int u_prec = -1;                   // precision of the last solve (for npb_potential)
+    npb::LegDev *d_legs[2] = {};       // device leg tables by precision
+    npb::LegDev h_legs[2][4];
+    std::string legs_key[2];
+    double *d_result = nullptr;
+    double *h_result = nullptr;  // pinned
+    void *d_scratch = nullptr;   // charge-list scratch (kept for re-running set-up)
+    size_t scratch_bytes = 0;
+    npb::ChargeScratch sc{};
+    std::vector<npb::Alloc> allocs;
+    std::vector<npb::GraphCache> graphs;
+};
+
+namespace npb {
+using Grid = ::npb_grid;
+
+extern const int kLegSlot[4];
+
+int grid_build(Ctx *ctx, const npb_problem *p, cudaStream_t st, Grid **out);
+void grid_free(Grid *g);
+int grid_setup(Grid *g, cudaStream_t st);
+int grid_boundary(Grid *g, int medium, int prec, cudaStream_t st, const double **out);
+int grid_half_masks(Grid *g, cudaStream_t st);
+int grid_states(Grid *g, int prec, cudaStream_t st);
+int grid_prepare(Grid *g, const npb_opts *o, cudaStream_t st);
+LegDev make_leg(const Grid *g, int leg, const npb_opts *o);
+SweepShape shape_for(Ctx *ctx, int prec, int dir, int n);
+int run_step(Grid *g, int prec, int scheme, int slot0, int n_legs, cudaStream_t st);
+int init_legs(Grid *g, int prec, const int *legs, int n, cudaStream_t st);
+int enqueue_energy(Grid *g, const npb_opts *o, cudaStream_t st);
+void serve_shutdown(Ctx *ctx);
+
+}  // namespace npb
+

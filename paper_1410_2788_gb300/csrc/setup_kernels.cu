@@ -1,0 +1,420 @@
+// setup_kernels.cu -- per-grid set-up on the device (run once per molecule).
+//
+//   mask        node bits of Omega_m: a node is inside iff it lies on or inside some
+//               atom's ball (Sec. 3.1: eps_m "on/inside" the surface).  For the midpoint
+//               eps reading, the same test on the half points p + e_d/2.
+//   charges     the trilinear spread of the point charges (Sec. 3.1, Eq. RhoEq) as a
+//               list of (node, qtilde) entries grouped by x-line.  Built without
+//               order-dependent floating-point atomics: entries are bucketed by line,
+//               sorted by (x, atom, corner) and summed in that fixed order.
+//   boundary    Eq. (BoundaryCond) on the 6 faces: solvent uses eps_out and kbar,
+//               vacuum eps_in and kbar = 0.  FP64 pair terms, or FP32 pair terms with
+//               per-chunk FP64 accumulation for the mixed-precision path.
+//
+// The distance tests and weights use explicitly rounded FP64 operations (no fused
+// multiply-add), so that inside/outside decisions and node charges are reproducible.
+#include "npb_internal.cuh"
+#include "setup_kernels.cuh"
+
+namespace npb {
+
+__device__ __forceinline__ double node_coord(double o, int i, double h) {
+    return __dadd_rn(o, __dmul_rn((double)i, h));
+}
+
+__device__ __forceinline__ double dist2(double dx, double dy, double dz) {
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// One block per atom; threads walk the atom's bounding box of nodes.
+__global__ void k_mask_atoms(GridGeom g, const double *__restrict__ xyz,
+                             const double *__restrict__ radius, int n_atoms,
+                             uint32_t *__restrict__ mask, uint32_t *__restrict__ hx,
+                             uint32_t *__restrict__ hy, uint32_t *__restrict__ hz) {
+    const int a = blockIdx.x;
+    if (a >= n_atoms) return;
+    const double c[3] = {xyz[3 * a], xyz[3 * a + 1], xyz[3 * a + 2]};
+    const double rho = radius[a];
+    const double r2 = __dmul_rn(rho, rho);
+    const int n[3] = {g.nx, g.ny, g.nz};
+    const double o[3] = {g.ox, g.oy, g.oz};
+    int lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = (int)floor((c[d] - rho - o[d]) / g.h) - 1;
+        hi[d] = (int)ceil((c[d] + rho - o[d]) / g.h) + 1;
+        lo[d] = max(lo[d], 0);
+        hi[d] = min(hi[d], n[d] - 1);
+    }
+    const int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1, ez = hi[2] - lo[2] + 1;
+    if (ex <= 0 || ey <= 0 || ez <= 0) return;
+    const int total = ex * ey * ez;
+    const int wpr = g.pitch >> 5;
+    const double hh = __dmul_rn(0.5, g.h);
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int i = lo[0] + t % ex;
+        const int j = lo[1] + (t / ex) % ey;
+        const int k = lo[2] + t / (ex * ey);
+        const double px = node_coord(o[0], i, g.h), py = node_coord(o[1], j, g.h),
+                     pz = node_coord(o[2], k, g.h);
+        const int64_t w = ((int64_t)k * g.ny + j) * wpr + (i >> 5);
+        const uint32_t bit = 1u << (i & 31);
+        if (dist2(__dsub_rn(px, c[0]), __dsub_rn(py, c[1]), __dsub_rn(pz, c[2])) <= r2)
+            atomicOr(mask + w, bit);
+        if (hx) {
+            if (dist2(__dsub_rn(__dadd_rn(px, hh), c[0]), __dsub_rn(py, c[1]), __dsub_rn(pz, c[2])) <= r2)
+                atomicOr(hx + w, bit);
+            if (dist2(__dsub_rn(px, c[0]), __dsub_rn(__dadd_rn(py, hh), c[1]), __dsub_rn(pz, c[2])) <= r2)
+                atomicOr(hy + w, bit);
+            if (dist2(__dsub_rn(px, c[0]), __dsub_rn(py, c[1]), __dsub_rn(__dadd_rn(pz, hh), c[2])) <= r2)
+                atomicOr(hz + w, bit);
+        }
+    }
+}
+
+// Raw trilinear entries: thread per (atom, corner).
+__global__ void k_charge_raw(GridGeom g, const double *__restrict__ xyz, const double *__restrict__ q,
+                             int n_atoms, RawEntry *__restrict__ raw, int32_t *__restrict__ count) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 8 * n_atoms) return;
+    const int a = e >> 3, corner = e & 7;
+    const double o[3] = {g.ox, g.oy, g.oz};
+    int i0[3];
+    double f[3];
+    for (int d = 0; d < 3; ++d) {
+        const double s = __ddiv_rn(__dsub_rn(xyz[3 * a + d], o[d]), g.h);
+        i0[d] = (int)floor(s);
+        f[d] = __dsub_rn(s, (double)i0[d]);
+    }
+    const int ox = corner & 1, oy = (corner >> 1) & 1, oz = (corner >> 2) & 1;
+    const double wx = ox ? f[0] : __dsub_rn(1.0, f[0]);
+    const double wy = oy ? f[1] : __dsub_rn(1.0, f[1]);
+    const double wz = oz ? f[2] : __dsub_rn(1.0, f[2]);
+    const double w = __dmul_rn(__dmul_rn(wx, wy), wz);
+    RawEntry r;
+    r.x = i0[0] + ox;
+    r.line = (i0[2] + oz) * g.ny + (i0[1] + oy);
+    r.key = e;
+    r.val = __dmul_rn(q[a], w);
+    raw[e] = r;
+    atomicAdd(count + r.line, 1);
+}
+
+// Exclusive scan of count[0..n) into begin[] (and the sum into *total); one block of 1024 threads.
+__global__ void k_scan_lines(const int32_t *__restrict__ count, int32_t *__restrict__ begin, int n,
+                             int32_t *__restrict__ total) {
+    __shared__ int32_t part[1024];
+    const int t = threadIdx.x;
+    const int per = (n + blockDim.x - 1) / blockDim.x;
+    const int lo = min(n, t * per), hi = min(n, lo + per);
+    int32_t s = 0;
+    for (int i = lo; i < hi; ++i) s += count[i];
+    part[t] = s;
+    __syncthreads();
+    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+        const int32_t v = t >= off ? part[t - off] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int32_t run = t > 0 ? part[t - 1] : 0;
+    for (int i = lo; i < hi; ++i) {
+        begin[i] = run;
+        run += count[i];
+    }
+    if (total && t == (int)blockDim.x - 1) *total = part[t];
+}
+
+__global__ void k_charge_scatter(const RawEntry *__restrict__ raw, int n_raw,
+                                 const int32_t *__restrict__ begin, int32_t *__restrict__ fill,
+                                 RawEntry *__restrict__ bucket) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_raw) return;
+    const RawEntry r = raw[e];
+    const int pos = begin[r.line] + atomicAdd(fill + r.line, 1);
+    bucket[pos] = r;
+}
+
+// Thread per line: sort the line's bucket by (x, key), sum equal x in that order, and
+// write the merged entries back to the front of the bucket.
+__global__ void k_charge_merge(RawEntry *__restrict__ bucket, const int32_t *__restrict__ begin,
+                               const int32_t *__restrict__ count, int32_t *__restrict__ out_count,
+                               int n_lines) {
+    const int ln = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ln >= n_lines) return;
+    const int b = begin[ln], c = count[ln];
+    RawEntry *v = bucket + b;
+    for (int i = 1; i < c; ++i) {  // insertion sort; buckets hold a few dozen entries
+        const RawEntry t = v[i];
+        int j = i - 1;
+        while (j >= 0 && (v[j].x > t.x || (v[j].x == t.x && v[j].key > t.key))) {
+            v[j + 1] = v[j];
+            --j;
+        }
+        v[j + 1] = t;
+    }
+    int m = 0;
+    for (int i = 0; i < c;) {
+        const int x = v[i].x;
+        double s = 0.0;
+        while (i < c && v[i].x == x) s = __dadd_rn(s, v[i++].val);
+        v[m].x = x;
+        v[m].val = s;
+        ++m;
+    }
+    out_count[ln] = m;
+}
+
+// Thread per line: copy the merged entries into the final, contiguous charge list.
+__global__ void k_charge_compact(GridGeom g, const RawEntry *__restrict__ bucket,
+                                 const int32_t *__restrict__ raw_begin, const int32_t *__restrict__ begin,
+                                 const int32_t *__restrict__ count, int32_t *__restrict__ ent_x,
+                                 double *__restrict__ ent_qt, int64_t *__restrict__ ent_off, int n_lines) {
+    const int ln = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ln >= n_lines) return;
+    const int rb = raw_begin[ln], b = begin[ln], c = count[ln];
+    const int y = ln % g.ny, z = ln / g.ny;
+    for (int i = 0; i < c; ++i) {
+        const RawEntry r = bucket[rb + i];
+        ent_x[b + i] = r.x;
+        ent_qt[b + i] = r.val;
+        ent_off[b + i] = ((int64_t)z * g.ny + y) * g.pitch + r.x;
+    }
+}
+
+// Face enumeration: f0 z=0 (nx*ny), f1 z=nz-1, f2 y=0 (nx*(nz-2)), f3 y=ny-1,
+// f4 x=0 ((ny-2)*(nz-2)), f5 x=nx-1.
+__host__ __device__ int64_t face_count(int nx, int ny, int nz) {
+    return 2LL * nx * ny + 2LL * nx * (nz - 2) + 2LL * (ny - 2) * (nz - 2);
+}
+
+__device__ __forceinline__ void face_node(int64_t f, int nx, int ny, int nz, int &i, int &j, int &k) {
+    const int64_t A = (int64_t)nx * ny, B = (int64_t)nx * (nz - 2), Cc = (int64_t)(ny - 2) * (nz - 2);
+    if (f < 2 * A) {
+        k = f < A ? 0 : nz - 1;
+        const int64_t r = f % A;
+        i = (int)(r % nx);
+        j = (int)(r / nx);
+    } else if (f < 2 * A + 2 * B) {
+        const int64_t ff = f - 2 * A;
+        j = ff < B ? 0 : ny - 1;
+        const int64_t r = ff % B;
+        i = (int)(r % nx);
+        k = 1 + (int)(r / nx);
+    } else {
+        const int64_t ff = f - 2 * A - 2 * B;
+        i = ff < Cc ? 0 : nx - 1;
+        const int64_t r = ff % Cc;
+        j = 1 + (int)(r % (ny - 2));
+        k = 1 + (int)(r / (ny - 2));
+    }
+}
+
+constexpr int kAtomChunk = 256;
+
+// FP64 pair terms, summed in atom order: C sum_i q_i exp(-kbar d / sqrt(eps)) / (eps d).
+__global__ void k_boundary_f64(GridGeom g, const double *__restrict__ xyz, const double *__restrict__ q,
+                               int n_atoms, double eps, double kbar, double *__restrict__ out) {
+    __shared__ double sa[kAtomChunk][4];
+    const int64_t nf = face_count(g.nx, g.ny, g.nz);
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int i = 0, j = 0, k = 0;
+    if (f < nf) face_node(f, g.nx, g.ny, g.nz, i, j, k);
+    const double x = node_coord(g.ox, i, g.h), y = node_coord(g.oy, j, g.h), z = node_coord(g.oz, k, g.h);
+    const double ks = kbar / sqrt(eps);
+    double s = 0.0;
+    for (int a0 = 0; a0 < n_atoms; a0 += kAtomChunk) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < kAtomChunk && a0 + t < n_atoms; t += blockDim.x) {
+            sa[t][0] = xyz[3 * (a0 + t)];
+            sa[t][1] = xyz[3 * (a0 + t) + 1];
+            sa[t][2] = xyz[3 * (a0 + t) + 2];
+            sa[t][3] = q[a0 + t];
+        }
+        __syncthreads();
+        const int na = min(kAtomChunk, n_atoms - a0);
+        for (int t = 0; t < na; ++t) {
+            const double dx = x - sa[t][0], dy = y - sa[t][1], dz = z - sa[t][2];
+            const double d = sqrt(dx * dx + dy * dy + dz * dz);
+            s += sa[t][3] * exp(-ks * d) / (eps * d);
+        }
+    }
+    if (f < nf) out[f] = kBjerrum * s;
+}
+
+// FP32 pair terms, each chunk summed in FP32 and chunks accumulated in FP64.
+__global__ void k_boundary_f32(GridGeom g, const double *__restrict__ xyz, const double *__restrict__ q,
+                               int n_atoms, double eps, double kbar, double *__restrict__ out) {
+    __shared__ float sa[kAtomChunk][4];
+    const int64_t nf = face_count(g.nx, g.ny, g.nz);
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int i = 0, j = 0, k = 0;
+    if (f < nf) face_node(f, g.nx, g.ny, g.nz, i, j, k);
+    // positions relative to the grid origin keep FP32 resolution near 1e-5 A
+    const float x = (float)(i * g.h), y = (float)(j * g.h), z = (float)(k * g.h);
+    const float ks = (float)(kbar / sqrt(eps));
+    const float ieps = (float)(1.0 / eps);
+    double s = 0.0;
+    for (int a0 = 0; a0 < n_atoms; a0 += kAtomChunk) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < kAtomChunk && a0 + t < n_atoms; t += blockDim.x) {
+            sa[t][0] = (float)(xyz[3 * (a0 + t)] - g.ox);
+            sa[t][1] = (float)(xyz[3 * (a0 + t) + 1] - g.oy);
+            sa[t][2] = (float)(xyz[3 * (a0 + t) + 2] - g.oz);
+            sa[t][3] = (float)q[a0 + t];
+        }
+        __syncthreads();
+        const int na = min(kAtomChunk, n_atoms - a0);
+        float part = 0.f;
+        for (int t = 0; t < na; ++t) {
+            const float dx = x - sa[t][0], dy = y - sa[t][1], dz = z - sa[t][2];
+            const float d2 = dx * dx + dy * dy + dz * dz;
+            const float id = rsqrtf(d2);
+            part += sa[t][3] * __expf(-ks * d2 * id) * id;
+        }
+        s += (double)part;
+    }
+    if (f < nf) out[f] = kBjerrum * (double)ieps * s;
+}
+
+// Zero interior, Dirichlet faces, zero padding: the initial state of a leg (Sec. 2.2).
+template <typename T>
+__global__ void k_init_leg(GridGeom g, const double *__restrict__ bc, T *__restrict__ u) {
+    const int64_t total = (int64_t)g.nz * g.ny * g.pitch;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(p % g.pitch);
+        const int64_t r = p / g.pitch;
+        const int j = (int)(r % g.ny), k = (int)(r / g.ny);
+        T v = T(0);
+        if (i < g.nx) {
+            const bool face = i == 0 || j == 0 || k == 0 || i == g.nx - 1 || j == g.ny - 1 || k == g.nz - 1;
+            if (face) {
+                const int64_t A = (int64_t)g.nx * g.ny, B = (int64_t)g.nx * (g.nz - 2),
+                              Cc = (int64_t)(g.ny - 2) * (g.nz - 2);
+                int64_t f;
+                if (k == 0 || k == g.nz - 1) f = (k == 0 ? 0 : A) + (int64_t)j * g.nx + i;
+                else if (j == 0 || j == g.ny - 1) f = 2 * A + (j == 0 ? 0 : B) + (int64_t)(k - 1) * g.nx + i;
+                else f = 2 * A + 2 * B + (i == 0 ? 0 : Cc) + (int64_t)(k - 1) * (g.ny - 2) + (j - 1);
+                v = (T)bc[f];
+            }
+        }
+        u[p] = v;
+    }
+}
+
+// Dense FP64 copy of a padded state (for export / potential read-back).
+template <typename T>
+__global__ void k_unpad(GridGeom g, const T *__restrict__ u, double *__restrict__ out) {
+    const int64_t total = (int64_t)g.nz * g.ny * g.nx;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(p % g.nx);
+        const int64_t r = p / g.nx;
+        out[p] = (double)u[r * g.pitch + i];
+    }
+}
+
+template <typename T>
+__global__ void k_pad(GridGeom g, const double *__restrict__ in, T *__restrict__ u) {
+    const int64_t total = (int64_t)g.nz * g.ny * g.nx;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(p % g.nx);
+        const int64_t r = p / g.nx;
+        u[r * g.pitch + i] = (T)in[p];
+    }
+}
+
+__global__ void k_mask_dense(GridGeom g, const uint32_t *__restrict__ mask, uint8_t *__restrict__ out) {
+    const int64_t total = (int64_t)g.nz * g.ny * g.nx;
+    const int wpr = g.pitch >> 5;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(p % g.nx);
+        const int64_t r = p / g.nx;
+        out[p] = (uint8_t)((mask[r * wpr + (i >> 5)] >> (i & 31)) & 1u);
+    }
+}
+
+__global__ void k_qt_dense(GridGeom g, const int32_t *__restrict__ line_begin,
+                           const int32_t *__restrict__ line_count, const int32_t *__restrict__ ent_x,
+                           const double *__restrict__ ent_qt, double *__restrict__ out) {
+    const int ln = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ln >= g.ny * g.nz) return;
+    const int b = line_begin[ln], c = line_count[ln];
+    for (int e = b; e < b + c; ++e) out[(int64_t)ln * g.nx + ent_x[e]] = ent_qt[e];
+}
+
+// ---------------------------------------------------------------- host launchers
+static inline int blocks_for(int64_t n, int t) { return (int)std::min<int64_t>((n + t - 1) / t, 1 << 20); }
+
+cudaError_t setup_mask(const GridGeom &g, const double *xyz, const double *radius, int n_atoms,
+                       uint32_t *mask, uint32_t *hx, uint32_t *hy, uint32_t *hz, cudaStream_t st) {
+    if (n_atoms > 0) k_mask_atoms<<<n_atoms, 256, 0, st>>>(g, xyz, radius, n_atoms, mask, hx, hy, hz);
+    return cudaGetLastError();
+}
+
+cudaError_t setup_charges(const GridGeom &g, const double *xyz, const double *q, int n_atoms,
+                          ChargeScratch &s, int32_t *line_begin, int32_t *line_count, int32_t *ent_x,
+                          double *ent_qt, int64_t *ent_off, cudaStream_t st) {
+    const int n_lines = g.ny * g.nz;
+    const int n_raw = 8 * n_atoms;
+    cudaMemsetAsync(s.count, 0, sizeof(int32_t) * n_lines, st);
+    cudaMemsetAsync(s.fill, 0, sizeof(int32_t) * n_lines, st);
+    if (n_raw > 0) k_charge_raw<<<blocks_for(n_raw, 256), 256, 0, st>>>(g, xyz, q, n_atoms, s.raw, s.count);
+    k_scan_lines<<<1, 1024, 0, st>>>(s.count, s.raw_begin, n_lines, nullptr);
+    if (n_raw > 0)
+        k_charge_scatter<<<blocks_for(n_raw, 256), 256, 0, st>>>(s.raw, n_raw, s.raw_begin, s.fill, s.bucket);
+    k_charge_merge<<<blocks_for(n_lines, 128), 128, 0, st>>>(s.bucket, s.raw_begin, s.count, line_count,
+                                                             n_lines);
+    k_scan_lines<<<1, 1024, 0, st>>>(line_count, line_begin, n_lines, s.total);
+    k_charge_compact<<<blocks_for(n_lines, 128), 128, 0, st>>>(g, s.bucket, s.raw_begin, line_begin, line_count,
+                                                               ent_x, ent_qt, ent_off, n_lines);
+    return cudaGetLastError();
+}
+
+cudaError_t setup_boundary(const GridGeom &g, const double *xyz, const double *q, int n_atoms, double eps,
+                           double kbar, bool fp32_pairs, double *out, cudaStream_t st) {
+    const int64_t nf = face_count(g.nx, g.ny, g.nz);
+    const int t = 128;
+    if (fp32_pairs) k_boundary_f32<<<blocks_for(nf, t), t, 0, st>>>(g, xyz, q, n_atoms, eps, kbar, out);
+    else k_boundary_f64<<<blocks_for(nf, t), t, 0, st>>>(g, xyz, q, n_atoms, eps, kbar, out);
+    return cudaGetLastError();
+}
+
+cudaError_t init_leg(int prec, const GridGeom &g, const double *bc, void *u, cudaStream_t st) {
+    const int64_t total = (int64_t)g.nz * g.ny * g.pitch;
+    const int t = 256;
+    const int b = std::min<int64_t>((total + t - 1) / t, 152 * 16);
+    if (prec == 0) k_init_leg<double><<<b, t, 0, st>>>(g, bc, (double *)u);
+    else k_init_leg<float><<<b, t, 0, st>>>(g, bc, (float *)u);
+    return cudaGetLastError();
+}
+
+cudaError_t unpad_state(int prec, const GridGeom &g, const void *u, double *out, cudaStream_t st) {
+    const int t = 256, b = 152 * 8;
+    if (prec == 0) k_unpad<double><<<b, t, 0, st>>>(g, (const double *)u, out);
+    else k_unpad<float><<<b, t, 0, st>>>(g, (const float *)u, out);
+    return cudaGetLastError();
+}
+
+cudaError_t pad_state(int prec, const GridGeom &g, const double *in, void *u, cudaStream_t st) {
+    const int t = 256, b = 152 * 8;
+    if (prec == 0) k_pad<double><<<b, t, 0, st>>>(g, in, (double *)u);
+    else k_pad<float><<<b, t, 0, st>>>(g, in, (float *)u);
+    return cudaGetLastError();
+}
+
+cudaError_t mask_dense(const GridGeom &g, const uint32_t *mask, uint8_t *out, cudaStream_t st) {
+    k_mask_dense<<<152 * 8, 256, 0, st>>>(g, mask, out);
+    return cudaGetLastError();
+}
+
+cudaError_t qt_dense(const GridGeom &g, const int32_t *line_begin, const int32_t *line_count,
+                     const int32_t *ent_x, const double *ent_qt, double *out, cudaStream_t st) {
+    const int n_lines = g.ny * g.nz;
+    k_qt_dense<<<blocks_for(n_lines, 128), 128, 0, st>>>(g, line_begin, line_count, ent_x, ent_qt, out);
+    return cudaGetLastError();
+}
+
+}  // namespace npb

@@ -1,0 +1,111 @@
+// stage_kernels.cu -- stand-alone LOD stages and the energy reduction.
+//
+//   nonlinear   Eq. (ana3) at every interior solvent node (used on its own by the
+//               row-level interface; inside a step it is fused into a sweep)
+//   source      Eq. (LODIE1_5): u += tau Q over the charge entries (LODIE1 ends on it)
+//   energy      Eqs. (rich) and (deltaG3): the FP64 charge-weighted sum over the
+//               charge nodes of the Richardson-combined solvent minus vacuum potential,
+//               reduced in a fixed order (one block, fixed tree), so the value does not
+//               depend on scheduling.
+#include "npb_internal.cuh"
+#include "sweep_kernel.cuh"
+
+namespace npb {
+
+template <typename T>
+__global__ void k_nonlinear(const LegDev *__restrict__ legs) {
+    const LegDev *lg = legs + blockIdx.z;
+    if (!lg->nl_on) return;
+    T *u = static_cast<T *>(lg->u);
+    const int nx = lg->nx, ny = lg->ny, nz = lg->nz, pitch = lg->pitch, wpr = pitch >> 5;
+    const int64_t total = (int64_t)(nz - 2) * (ny - 2) * (nx - 2);
+    const T q = (T)lg->nl_q, omq = (T)lg->nl_omq;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int i = 1 + (int)(p % (nx - 2));
+        const int64_t r = p / (nx - 2);
+        const int j = 1 + (int)(r % (ny - 2)), k = 1 + (int)(r / (ny - 2));
+        const int64_t row = (int64_t)k * ny + j;
+        const bool inside = lg->mask ? ((lg->mask[row * wpr + (i >> 5)] >> (i & 31)) & 1u) : true;
+        if (!inside) u[row * pitch + i] = nl_flow(u[row * pitch + i], q, omq);
+    }
+}
+
+template <typename T>
+__global__ void k_source(const LegDev *__restrict__ legs) {
+    const LegDev *lg = legs + blockIdx.z;
+    T *u = static_cast<T *>(lg->u);
+    const int ny = lg->ny, nz = lg->nz;
+    const int n_lines = ny * nz;
+    for (int ln = blockIdx.x * blockDim.x + threadIdx.x; ln < n_lines; ln += gridDim.x * blockDim.x) {
+        const int y = ln % ny, z = ln / ny;
+        if (y < 1 || y > ny - 2 || z < 1 || z > nz - 2) continue;
+        const int b = lg->line_begin[ln], c = lg->line_count[ln];
+        for (int e = b; e < b + c; ++e) {
+            const int64_t p = (int64_t)ln * lg->pitch + lg->ent_x[e];
+            u[p] += (T)(lg->src * lg->ent_qt[e]);
+        }
+    }
+}
+
+cudaError_t launch_nonlinear(int prec, const LegDev *legs, int n_legs, int nx, int ny, int nz,
+                             cudaStream_t st) {
+    dim3 grid(152 * 4, 1, n_legs);
+    if (prec == 0) k_nonlinear<double><<<grid, 256, 0, st>>>(legs);
+    else k_nonlinear<float><<<grid, 256, 0, st>>>(legs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_source(int prec, const LegDev *legs, int n_legs, int ny, int nz, cudaStream_t st) {
+    dim3 grid((ny * nz + 255) / 256, 1, n_legs);
+    if (prec == 0) k_source<double><<<grid, 256, 0, st>>>(legs);
+    else k_source<float><<<grid, 256, 0, st>>>(legs);
+    return cudaGetLastError();
+}
+
+// dG = 1/2 kT sum_e qt_e * combo_e, combo = (2 s_half - s_tau) - (2 v_half - v_tau) with
+// Richardson, else s_tau - v_tau.  legs: s_tau, s_half, v_tau, v_half element pointers.
+template <typename T>
+__global__ void k_energy(const T *__restrict__ s_tau, const T *__restrict__ s_half,
+                         const T *__restrict__ v_tau, const T *__restrict__ v_half,
+                         const int64_t *__restrict__ off, const double *__restrict__ qt,
+                         const int32_t *__restrict__ n_ent_dev, int richardson, double *__restrict__ out) {
+    __shared__ double part[1024];
+    const int n_ent = *n_ent_dev;
+    double acc = 0.0;
+    for (int e = threadIdx.x; e < n_ent; e += blockDim.x) {
+        const int64_t p = off[e];
+        double us, uv;
+        if (richardson) {
+            us = 2.0 * (double)s_half[p] - (double)s_tau[p];
+            uv = 2.0 * (double)v_half[p] - (double)v_tau[p];
+        } else {
+            us = (double)s_tau[p];
+            uv = (double)v_tau[p];
+        }
+        acc += qt[e] * (us - uv);
+    }
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) part[threadIdx.x] += part[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = 0.5 * kKT * part[0];
+}
+
+cudaError_t launch_energy(int prec, const void *s_tau, const void *s_half, const void *v_tau,
+                          const void *v_half, const int64_t *off, const double *qt, const int32_t *n_ent,
+                          int richardson, double *out, cudaStream_t st) {
+    if (prec == 0)
+        k_energy<double><<<1, 1024, 0, st>>>((const double *)s_tau, (const double *)s_half,
+                                             (const double *)v_tau, (const double *)v_half, off, qt,
+                                             n_ent, richardson, out);
+    else
+        k_energy<float><<<1, 1024, 0, st>>>((const float *)s_tau, (const float *)s_half,
+                                            (const float *)v_tau, (const float *)v_half, off, qt, n_ent,
+                                            richardson, out);
+    return cudaGetLastError();
+}
+
+}  // namespace npb

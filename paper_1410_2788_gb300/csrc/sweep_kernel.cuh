@@ -1,0 +1,398 @@
+// sweep_kernel.cuh -- one batch of implicit-Euler LOD line solves (Eqs. LODIE1_2-LODIE1_4).
+//
+// For direction d every interior grid line carries the tridiagonal system
+//     -r e_{-} v_{g-1} + (1 + r(e_{-} + e_{+})) v_g - r e_{+} v_{g+1} = w_g,   r = tau/h^2,
+// with eps at the half points (Eq. SpatialOperators).  The two face nodes of the line,
+// and the padding rows past its end, enter as identity rows, so they keep their values
+// and their coupling to the first/last interior unknown is exact.
+//
+// Line solver (a Thomas / parallel-cyclic-reduction hybrid): a line of up to SEG*L rows
+// is cut into SEG segments of L consecutive rows; one thread owns one segment in
+// registers.
+//   1. Local modified Thomas: for the rows strictly inside the segment,
+//      x_k = alpha_k + beta_k F + gamma_k E, where F and E are the segment's own first
+//      and last unknowns.
+//   2. Substituting this into the segment's first and last rows gives two rows per
+//      segment coupling (E_{s-1}, F_s, E_s) and (F_s, E_s, F_{s+1}).  Eliminating the
+//      F's leaves one tridiagonal row per segment in the E's, solved by PCR across the
+//      SEG threads of the line (log2 SEG rounds in shared memory).
+//   3. F_s follows from E_{s-1}, E_s; every interior row is one fused multiply-add pair.
+// The reduced systems are Schur complements of strictly diagonally dominant matrices,
+// so no step needs pivoting.
+//
+// Thread block: TX lines x SEG segments (threadIdx.x = line, threadIdx.y = segment).
+//   Y / Z sweeps: the TX lines are x-adjacent, so each row load/store of a warp is one
+//   contiguous run of TX elements; no staging.
+//   X sweep: the line runs along the unit-stride axis; the block stages its TX x-rows
+//   with 16-byte vector loads into a shared tile whose row stride is odd (bank-conflict
+//   free column access), and writes them back the same way.
+// Fused stages: FUSE_PRE_SRC adds tau Q to the staged x-rows (LODIE2 stage S),
+// FUSE_PRE_NL applies the nonlinear stage to the loaded x-rows (LODIE1 stage N),
+// FUSE_POST_NL applies it before the z-sweep store (LODIE2 stage N).
+#pragma once
+#include "npb_internal.cuh"
+
+namespace npb {
+
+template <typename T>
+__device__ __forceinline__ T fast_rcp(T x);
+template <>
+__device__ __forceinline__ float fast_rcp<float>(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+template <>
+__device__ __forceinline__ double fast_rcp<double>(double x) {
+    return 1.0 / x;
+}
+
+__device__ __forceinline__ float t_expm1(float x) { return expm1f(x); }
+__device__ __forceinline__ double t_expm1(double x) { return expm1(x); }
+__device__ __forceinline__ float t_log1p(float x) { return log1pf(x); }
+__device__ __forceinline__ double t_log1p(double x) { return log1p(x); }
+
+// The nonlinear stage of Eq. (ana3) in tanh form: tanh(w'/2) = q tanh(w/2), q =
+// exp(-kbar^2 tau).  With e = exp(-|w|), tanh(|w|/2) = (1-e)/(1+e) and
+// 1 - tanh(|w'|/2) = (1-q) + 2 q e/(1+e); then |w'| = log1p(2 t'/(1 - t')).  No term
+// overflows for any w and no step subtracts nearly equal numbers.
+template <typename T>
+__device__ __forceinline__ T nl_flow(T w, T q, T omq) {
+    const T aw = fabs(w);
+    const T em = t_expm1(-aw);  // e - 1
+    const T e = em + T(1);
+    const T inv = T(1) / (T(1) + e);
+    const T t = -q * em * inv;
+    const T omt = omq + T(2) * q * e * inv;
+    const T wn = t_log1p(T(2) * t / omt);
+    return copysign(wn, w);
+}
+
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+    using type = float4;
+    static constexpr int n = 4;
+};
+template <>
+struct Vec16<double> {
+    using type = double2;
+    static constexpr int n = 2;
+};
+
+__host__ __device__ __forceinline__ int sweep_tile_stride(int nx, int vec) {
+    const int nxv = (nx + vec - 1) / vec * vec;
+    return nxv | 1;
+}
+
+template <typename T, int DIR, int TX, int SEG>
+__host__ __device__ __forceinline__ size_t sweep_smem_bytes(int nx, int pitch) {
+    size_t b = (size_t)(4 + 8 + 1) * TX * SEG * sizeof(T);
+    if (DIR == DIR_X) {
+        const int S = sweep_tile_stride(nx, Vec16<T>::n);
+        b += (size_t)TX * S * sizeof(T);
+        b = (b + 15) & ~(size_t)15;
+        b += (size_t)2 * TX * (pitch / 32) * sizeof(uint32_t);
+    }
+    return b;
+}
+
+template <typename T, int DIR, int TX, int SEG, int L>
+__global__ void __launch_bounds__(TX *SEG)
+    sweep_kernel(const LegDev *__restrict__ legs, int flags) {
+    static_assert(L >= 2 && L <= 62, "segment length");
+    static_assert((SEG & (SEG - 1)) == 0, "SEG must be a power of two");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+
+    const LegDev *lg = legs + blockIdx.z;
+    const int nx = lg->nx, ny = lg->ny, nz = lg->nz, pitch = lg->pitch;
+    const int wpr = pitch >> 5;
+    const int line = threadIdx.x;
+    const int seg = threadIdx.y;
+    const int g0 = seg * L;
+    T *__restrict__ u = static_cast<T *>(lg->u);
+    const uint32_t *__restrict__ mask = lg->mask;
+    const int mid = lg->eps_mode;
+    const uint32_t *__restrict__ half = lg->half[DIR];
+    const int ndir = DIR == DIR_X ? nx : (DIR == DIR_Y ? ny : nz);
+    const T rE0 = (T)lg->rE[0], rE1 = (T)lg->rE[1], rE2 = (T)lg->rE[2];
+    const T nlq = (T)lg->nl_q, nlomq = (T)lg->nl_omq;
+    const bool nl_on = lg->nl_on != 0;
+
+    // ---- shared memory carve-up
+    T *red = reinterpret_cast<T *>(smem_raw);          // 13 * TX * SEG
+    T *fbuf = red;                                      // [SEG][TX][4]
+    T *pbuf = red + 4 * TX * SEG;                       // [2][SEG][TX][4]
+    T *ebuf = red + 12 * TX * SEG;                      // [SEG][TX]
+    T *tile = red + 13 * TX * SEG;                      // DIR_X: [TX][S]
+    const int S = sweep_tile_stride(nx, Vec16<T>::n);
+    uint32_t *smask = nullptr, *shalf = nullptr;
+    if (DIR == DIR_X) {
+        size_t off = (size_t)13 * TX * SEG * sizeof(T) + (size_t)TX * S * sizeof(T);
+        off = (off + 15) & ~(size_t)15;
+        smask = reinterpret_cast<uint32_t *>(smem_raw + off);
+        shalf = smask + TX * wpr;
+    }
+
+    // ---- this thread's line
+    int lx = 0, ly = 0, lz = 0;
+    bool active;
+    int64_t base, stride;
+    if (DIR == DIR_X) {
+        ly = 1 + blockIdx.x * TX + line;
+        lz = 1 + blockIdx.y;
+        active = ly <= ny - 2;
+        base = ((int64_t)lz * ny + ly) * pitch;
+        stride = 1;
+    } else if (DIR == DIR_Y) {
+        lx = blockIdx.x * TX + line;
+        lz = 1 + blockIdx.y;
+        active = lx >= 1 && lx <= nx - 2;
+        base = (int64_t)lz * ny * pitch + lx;
+        stride = pitch;
+    } else {
+        lx = blockIdx.x * TX + line;
+        ly = 1 + blockIdx.y;
+        active = lx >= 1 && lx <= nx - 2;
+        base = (int64_t)ly * pitch + lx;
+        stride = (int64_t)ny * pitch;
+    }
+
+    // ---- X sweep: stage the TX x-rows (and their mask words) in shared memory
+    if (DIR == DIR_X) {
+        constexpr int VEC = Vec16<T>::n;
+        using V = typename Vec16<T>::type;
+        const int nvec = (nx + VEC - 1) / VEC;
+        const int tid = threadIdx.y * TX + threadIdx.x;
+        const int nthr = TX * SEG;
+        const int y0 = 1 + blockIdx.x * TX;
+        for (int i = tid; i < TX * nvec; i += nthr) {
+            const int l = i / nvec, v = i - l * nvec;
+            const int y = y0 + l;
+            T vals[VEC];
+            if (y <= ny - 2) {
+                const V w = *reinterpret_cast<const V *>(u + ((int64_t)lz * ny + y) * pitch + v * VEC);
+                *reinterpret_cast<V *>(vals) = w;
+            } else {
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) vals[e] = T(0);
+            }
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) tile[l * S + v * VEC + e] = vals[e];
+        }
+        for (int i = tid; i < TX * wpr; i += nthr) {
+            const int l = i / wpr, w = i - l * wpr;
+            const int y = y0 + l;
+            const int64_t row = ((int64_t)lz * ny + (y <= ny - 2 ? y : 0)) * wpr + w;
+            smask[i] = mask ? __ldg(mask + row) : 0xffffffffu;
+            shalf[i] = (mid && half) ? __ldg(half + row) : 0u;
+        }
+        __syncthreads();
+        if (flags & FUSE_PRE_SRC) {
+            const double src = lg->src;
+            for (int l = tid; l < TX; l += nthr) {
+                const int y = y0 + l;
+                if (y > ny - 2) continue;
+                const int ln = lz * ny + y;
+                const int b = lg->line_begin[ln], c = lg->line_count[ln];
+                for (int e = b; e < b + c; ++e)
+                    tile[l * S + lg->ent_x[e]] += (T)(src * lg->ent_qt[e]);
+            }
+            __syncthreads();
+        }
+    }
+
+    // ---- node bits of rows g0-1 .. g0+L (bit k+1 <-> row g0+k), half bits likewise
+    uint64_t nb = 0, hb = 0;
+#pragma unroll
+    for (int k = -1; k <= L; ++k) {
+        const int g = g0 + k;
+        uint32_t bit = 1u, hbit = 0u;
+        if (g >= 0 && g < ndir && active) {
+            if (DIR == DIR_X) {
+                bit = (smask[line * wpr + (g >> 5)] >> (g & 31)) & 1u;
+                if (mid) hbit = (shalf[line * wpr + (g >> 5)] >> (g & 31)) & 1u;
+            } else {
+                const int64_t row = DIR == DIR_Y ? ((int64_t)lz * ny + g) : ((int64_t)g * ny + ly);
+                const int64_t w = row * wpr + (lx >> 5);
+                if (mask) bit = (__ldg(mask + w) >> (lx & 31)) & 1u;
+                if (mid && half) hbit = (__ldg(half + w) >> (lx & 31)) & 1u;
+            }
+        }
+        nb |= (uint64_t)bit << (k + 1);
+        hb |= (uint64_t)hbit << (k + 1);
+    }
+
+    // ---- load the segment's right-hand sides
+    T al[L], be[L], ga[L];
+#pragma unroll
+    for (int k = 0; k < L; ++k) {
+        const int g = g0 + k;
+        T v = T(0);
+        if (active && g < ndir) {
+            if (DIR == DIR_X) v = tile[line * S + g];
+            else v = u[base + (int64_t)g * stride];
+            if ((flags & FUSE_PRE_NL) && nl_on && g >= 1 && g <= ndir - 2 &&
+                ((nb >> (k + 1)) & 1u) == 0u)
+                v = nl_flow(v, nlq, nlomq);
+        }
+        al[k] = v;
+    }
+
+    auto coef = [&](int k, T &a, T &b, T &c) {
+        const int g = g0 + k;
+        if (g < 1 || g > ndir - 2) {
+            a = T(0);
+            b = T(1);
+            c = T(0);
+            return;
+        }
+        T em, ep;
+        if (mid) {
+            em = ((hb >> k) & 1u) ? rE2 : rE0;        // half point g - 1/2
+            ep = ((hb >> (k + 1)) & 1u) ? rE2 : rE0;  // half point g + 1/2
+        } else {
+            const uint32_t bm = (nb >> k) & 1u, b0 = (nb >> (k + 1)) & 1u, bp = (nb >> (k + 2)) & 1u;
+            const uint32_t im = bm + b0, ip = b0 + bp;
+            em = im == 2u ? rE2 : (im == 1u ? rE1 : rE0);
+            ep = ip == 2u ? rE2 : (ip == 1u ? rE1 : rE0);
+        }
+        a = -em;
+        c = -ep;
+        b = T(1) + em + ep;
+    };
+
+    // ---- 1. local modified Thomas
+    T a0, b0, c0, aL, bL, cL;
+    coef(0, a0, b0, c0);
+    coef(L - 1, aL, bL, cL);
+    T fa, fb, fc, fd, ea, eb, ec, ed;
+    if (L >= 3) {
+        T cp = T(0), ap = T(0), bp = T(1);
+#pragma unroll
+        for (int k = 1; k <= L - 2; ++k) {
+            T a, b, c;
+            coef(k, a, b, c);
+            const T m = fast_rcp(b - a * cp);
+            cp = c * m;
+            ap = (al[k] - a * ap) * m;
+            bp = -a * bp * m;
+            al[k] = ap;
+            be[k] = bp;
+            ga[k] = cp;
+        }
+        ga[L - 2] = -ga[L - 2];
+#pragma unroll
+        for (int k = L - 3; k >= 1; --k) {
+            const T cpk = ga[k];
+            al[k] = al[k] - cpk * al[k + 1];
+            be[k] = be[k] - cpk * be[k + 1];
+            ga[k] = -cpk * ga[k + 1];
+        }
+        fa = a0;
+        fb = b0 + c0 * be[1];
+        fc = c0 * ga[1];
+        fd = al[0] - c0 * al[1];
+        ea = aL * be[L - 2];
+        eb = bL + aL * ga[L - 2];
+        ec = cL;
+        ed = al[L - 1] - aL * al[L - 2];
+    } else {
+        fa = a0; fb = b0; fc = c0; fd = al[0];
+        ea = aL; eb = bL; ec = cL; ed = al[L - 1];
+    }
+
+    // ---- 2. reduced system in the segment ends
+    const int me = seg * TX + line;
+    fbuf[4 * me + 0] = fa;
+    fbuf[4 * me + 1] = fb;
+    fbuf[4 * me + 2] = fc;
+    fbuf[4 * me + 3] = fd;
+    __syncthreads();
+    const T ifb = fast_rcp(fb);
+    T A = -ea * fa * ifb;
+    T B = eb - ea * fc * ifb;
+    T C = T(0);
+    T D = ed - ea * fd * ifb;
+    if (seg + 1 < SEG) {
+        const int nx_ = (seg + 1) * TX + line;
+        const T nfa = fbuf[4 * nx_ + 0], nfb = fbuf[4 * nx_ + 1], nfc = fbuf[4 * nx_ + 2],
+                nfd = fbuf[4 * nx_ + 3];
+        const T inb = fast_rcp(nfb);
+        B -= ec * nfa * inb;
+        C = -ec * nfc * inb;
+        D -= ec * nfd * inb;
+    }
+#pragma unroll
+    for (int st = 1, r = 0; st < SEG; st <<= 1, ++r) {
+        T *buf = pbuf + (r & 1) * 4 * TX * SEG;
+        buf[4 * me + 0] = A;
+        buf[4 * me + 1] = B;
+        buf[4 * me + 2] = C;
+        buf[4 * me + 3] = D;
+        __syncthreads();
+        T la = T(0), lb = T(1), lc = T(0), ld = T(0), ua = T(0), ub = T(1), uc = T(0), ud = T(0);
+        if (seg - st >= 0) {
+            const int o = 4 * ((seg - st) * TX + line);
+            la = buf[o]; lb = buf[o + 1]; lc = buf[o + 2]; ld = buf[o + 3];
+        }
+        if (seg + st < SEG) {
+            const int o = 4 * ((seg + st) * TX + line);
+            ua = buf[o]; ub = buf[o + 1]; uc = buf[o + 2]; ud = buf[o + 3];
+        }
+        const T k1 = A * fast_rcp(lb), k2 = C * fast_rcp(ub);
+        B = B - k1 * lc - k2 * ua;
+        D = D - k1 * ld - k2 * ud;
+        A = -k1 * la;
+        C = -k2 * uc;
+    }
+    const T E = D * fast_rcp(B);
+    ebuf[me] = E;
+    __syncthreads();
+    const T Eprev = seg > 0 ? ebuf[(seg - 1) * TX + line] : T(0);
+    const T F = (fd - fa * Eprev - fc * E) * ifb;
+
+    // ---- 3. expand and store the interior rows
+    if (DIR == DIR_X) {
+#pragma unroll
+        for (int k = 0; k < L; ++k) {
+            const int g = g0 + k;
+            if (active && g >= 1 && g <= ndir - 2) {
+                const T x = k == 0 ? F : (k == L - 1 ? E : al[k] + be[k] * F + ga[k] * E);
+                tile[line * S + g] = x;
+            }
+        }
+        __syncthreads();
+        constexpr int VEC = Vec16<T>::n;
+        using V = typename Vec16<T>::type;
+        const int nvec = (nx + VEC - 1) / VEC;
+        const int tid = threadIdx.y * TX + threadIdx.x;
+        const int y0 = 1 + blockIdx.x * TX;
+        for (int i = tid; i < TX * nvec; i += TX * SEG) {
+            const int l = i / nvec, v = i - l * nvec;
+            const int y = y0 + l;
+            if (y > ny - 2) continue;
+            T vals[VEC];
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) vals[e] = tile[l * S + v * VEC + e];
+            *reinterpret_cast<V *>(u + ((int64_t)lz * ny + y) * pitch + v * VEC) =
+                *reinterpret_cast<const V *>(vals);
+        }
+    } else {
+        if (active) {
+#pragma unroll
+            for (int k = 0; k < L; ++k) {
+                const int g = g0 + k;
+                if (g >= 1 && g <= ndir - 2) {
+                    T x = k == 0 ? F : (k == L - 1 ? E : al[k] + be[k] * F + ga[k] * E);
+                    if ((flags & FUSE_POST_NL) && nl_on && ((nb >> (k + 1)) & 1u) == 0u)
+                        x = nl_flow(x, nlq, nlomq);
+                    u[base + (int64_t)g * stride] = x;
+                }
+            }
+        }
+    }
+}
+
+}  // namespace npb

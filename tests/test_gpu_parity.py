@@ -1,0 +1,280 @@
+"""CUDA path against the CPU oracle, through the C ABI, on the same seeded inputs.
+
+Tolerances:
+  * FP64 path: relative Linf on u <= 1e-10 per leg, relative dG <= 1e-10.
+  * FP32-sweep path: relative Linf on u <= 1e-4 (the Eq. ErrorMeasure norm),
+    absolute <= 1e-4 kT/e on nodes at least 2h from every charge node,
+    relative dG <= 1e-4; the absolute error at charge nodes is reported.
+  * set-up: node mask bit-exact, trilinear charges bit-exact, face data 1e-12
+    (FP64 pair terms) relative.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import npb_inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def npb():
+    import paper_1410_2788_gb300 as m
+    from paper_1410_2788_gb300 import build
+
+    build.build()
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(npb):
+    c = npb.npb_ctx_create(0, 0)
+    yield c
+    npb.npb_ctx_destroy(c)
+
+
+@pytest.fixture(scope="module")
+def O(oracle_lib):
+    import os
+
+    oracle_lib.set_threads(os.cpu_count() or 8)
+    return oracle_lib
+
+
+def linf_rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def small_molecule(nx=37, ny=29, nz=23, h=0.5, kappa2=0.84):
+    """A hand-placed 8-atom molecule on a ragged, non-cubic grid (odd sizes, padded rows)."""
+    rng = np.random.default_rng(2024)
+    lo = np.array([3.0, 3.0, 3.0])
+    hi = np.array([(nx - 1) * h - 3.0, (ny - 1) * h - 3.0, (nz - 1) * h - 3.0])
+    xyz = lo + (hi - lo) * rng.random((8, 3))
+    return I.Problem(xyz=xyz, q=rng.uniform(-0.8, 0.8, 8), radius=rng.uniform(1.5, 2.0, 8), eps_in=1.0,
+                     eps_out=80.0, kappa2=kappa2, h=h, n=(nx, ny, nz), origin=(0.0, 0.0, 0.0), name="small")
+
+
+# ------------------------------------------------------------------------------ set-up
+@pytest.mark.parametrize("make", [lambda: I.born_sphere(0.84), small_molecule,
+                                  lambda: I.random_walk_molecule(300, 65, 0.5, seed=I.SEED_BASE + 70)])
+def test_setup_parity(npb, ctx, O, make):
+    p = make()
+    g = npb.npb_grid_create(ctx, p)
+    try:
+        shape = npb.grid_shape(p)
+        mask = npb.npb_grid_export(g, npb.NPB_EXPORT_MASK, shape)
+        assert np.array_equal(mask, O.mask_vdw(p))
+        qt = npb.npb_grid_export(g, npb.NPB_EXPORT_QTILDE, shape)
+        assert np.array_equal(qt, O.charge_spread(p))
+        for what, medium in [(npb.NPB_EXPORT_U0_SOLVENT, O.SOLVENT), (npb.NPB_EXPORT_U0_VACUUM, O.VACUUM)]:
+            u0 = npb.npb_grid_export(g, what, shape)
+            ref = np.zeros(shape)
+            O.boundary(p, medium, ref)
+            assert linf_rel(u0, ref) <= 1e-12
+    finally:
+        npb.npb_grid_destroy(g)
+
+
+# ------------------------------------------------------------------------------ single stages
+STAGES = ["SOURCE", "SWEEP_X", "SWEEP_Y", "SWEEP_Z", "NONLINEAR", "STEP"]
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 2e-5)])
+@pytest.mark.parametrize("leg", [0, 1, 2, 3])
+@pytest.mark.parametrize("scheme", [2, 1])
+def test_stage_parity(npb, ctx, O, precision, tol, leg, scheme):
+    p = small_molecule()
+    dt, alpha = 0.4, 1.0 / 25.0
+    tau = dt / alpha * (0.5 if leg in (1, 3) else 1.0)
+    medium = O.SOLVENT if leg in (0, 1) else O.VACUUM
+    st = O.setup(p, medium)
+    opts = npb.make_opts(dt, alpha, 1, scheme=scheme, precision=precision)
+    g = npb.npb_grid_create(ctx, p)
+    try:
+        rng = np.random.default_rng(leg + 10 * precision)
+        base = st.u0 + rng.normal(0, 4.0, st.u0.shape) * (st.u0 == 0)
+        base[st.u0 != 0] = st.u0[st.u0 != 0]
+        if precision == 1:
+            base = base.astype(np.float32).astype(np.float64)
+        for name in STAGES:
+            got = npb.npb_apply(g, opts, leg, getattr(npb, "NPB_OP_" + name), base)
+            ref = base.copy()
+            if name == "SOURCE":
+                O.source(ref, st.rho, tau)
+            elif name.startswith("SWEEP"):
+                d = "XYZ".index(name[-1])
+                O.sweep(ref, st.e_half[d], d, tau, p.h)
+            elif name == "NONLINEAR":
+                O.nonlinear(ref, st.kappa2_node, tau)
+            else:
+                O.lod_run(ref, st, tau, p.h, 1, scheme)
+            err = linf_rel(got, ref)
+            assert err <= tol, (name, err)
+            faces = np.ones(ref.shape, dtype=bool)
+            faces[1:-1, 1:-1, 1:-1] = False
+            assert np.array_equal(got[faces], base[faces]), name
+    finally:
+        npb.npb_grid_destroy(g)
+
+
+# ------------------------------------------------------------------------------ legs and energies
+def _born_opts(npb, precision=0, richardson=True):
+    # the Born configuration: dt = 0.1 with alpha = 1, 200 steps
+    return npb.make_opts(0.1, 1.0, 200, precision=precision, richardson=richardson)
+
+
+@pytest.mark.parametrize("kappa2", [0.0, 0.84])
+def test_born_legs_fp64(npb, ctx, O, kappa2):
+    p = I.born_sphere(kappa2)
+    opts = _born_opts(npb)
+    g = npb.npb_grid_create(ctx, p)
+    try:
+        for medium, leg in [(0, 0), (1, 2)]:
+            npb.npb_lod_solve(g, opts, medium, 1.0)
+            got = npb.npb_potential(g, leg, npb.grid_shape(p))
+            ref = O.lod_leg(p, medium, 0.1, 200)
+            assert linf_rel(got, ref) <= 1e-10
+        dg = npb.npb_energy(g, opts)
+        ref = O.energy(p, 0.1, 200, richardson=True)
+        assert abs(dg - ref) <= 1e-10 * abs(ref)
+    finally:
+        npb.npb_grid_destroy(g)
+
+
+def _charge_distance_mask(qt, h_nodes=2):
+    """True on nodes at least h_nodes grid steps (Chebyshev) from every charge node."""
+    near = np.zeros(qt.shape, dtype=bool)
+    idx = np.argwhere(qt != 0)
+    for k, j, i in idx:
+        near[max(0, k - h_nodes):k + h_nodes + 1, max(0, j - h_nodes):j + h_nodes + 1,
+             max(0, i - h_nodes):i + h_nodes + 1] = True
+    return ~near
+
+
+def _energy_case(npb, ctx, O, p, dt, alpha, n, richardson=True, eps_mode=0, scheme=2, check_fp32=True):
+    tau = dt / alpha
+    mode = "harmonic" if eps_mode == 0 else "midpoint"
+    ref_dg, ref_legs, st = O.energy(p, tau, n, richardson=richardson, scheme=scheme, eps_mode=mode,
+                                    return_legs=True)
+    g = npb.npb_grid_create(ctx, p)
+    report = {}
+    try:
+        names = {0: "solvent_tau", 1: "solvent_half", 2: "vacuum_tau", 3: "vacuum_half"}
+        legs = [0, 1, 2, 3] if richardson else [0, 2]
+        precisions = [0, 1] if check_fp32 else [0]
+        for prec in precisions:
+            opts = npb.make_opts(dt, alpha, n, scheme=scheme, richardson=richardson, precision=prec,
+                                 eps_mode=eps_mode)
+            dg = npb.npb_energy(g, opts)
+            rel = abs(dg - ref_dg) / abs(ref_dg)
+            report[prec] = {"dG": dg, "ref": ref_dg, "rel": rel}
+            assert rel <= (1e-10 if prec == 0 else 1e-4), (prec, dg, ref_dg)
+            far = _charge_distance_mask(st.qt)
+            for leg in legs:
+                got = npb.npb_potential(g, leg, npb.grid_shape(p))
+                ref = ref_legs[names[leg]]
+                e = linf_rel(got, ref)
+                assert e <= (1e-10 if prec == 0 else 1e-4), (prec, leg, e)
+                if prec == 1:
+                    far_abs = float(np.abs(got - ref)[far].max())
+                    at_q = float(np.abs(got - ref)[st.qt != 0].max())
+                    report[prec][f"leg{leg}"] = {"linf_rel": e, "abs_far": far_abs, "abs_at_charges": at_q}
+                    assert far_abs <= 1e-4 * max(1.0, float(np.abs(ref[far]).max())), (leg, far_abs)
+    finally:
+        npb.npb_grid_destroy(g)
+    return report
+
+
+def test_energy_born_both_kappa(npb, ctx, O):
+    for k2 in (0.0, 0.84):
+        _energy_case(npb, ctx, O, I.born_sphere(k2), 0.1, 1.0, 200)
+
+
+def test_energy_small_ragged_lodie1_and_midpoint(npb, ctx, O):
+    p = small_molecule()
+    _energy_case(npb, ctx, O, p, 0.4, 1.0 / 25.0, 10, scheme=1)
+    _energy_case(npb, ctx, O, p, 0.4, 1.0 / 25.0, 10, eps_mode=1)
+    _energy_case(npb, ctx, O, p, 0.4, 1.0 / 25.0, 10, richardson=False)
+
+
+def test_energy_protein_1k_129(npb, ctx, O):
+    """The 1,000-atom random-walk molecule on 129^3: RE+V at dt 0.4 / alpha 1/25, 25 steps."""
+    rep = _energy_case(npb, ctx, O, I.protein_1k(), 0.4, 1.0 / 25.0, 25)
+    print("protein_1k", rep)
+
+
+def test_energy_large_20k_257_fp32(npb, ctx, O):
+    """Full-size 257^3, 20,000 atoms, 40 Richardson-accelerated steps, FP32 sweeps."""
+    p = I.large_20k()
+    dt, alpha, n = 0.4, 1.0 / 25.0, 40
+    ref_dg = O.energy(p, dt / alpha, n)
+    g = npb.npb_grid_create(ctx, p)
+    try:
+        dg = npb.npb_energy(g, npb.make_opts(dt, alpha, n, precision=1))
+    finally:
+        npb.npb_grid_destroy(g)
+    print("large_20k", dg, ref_dg, abs(dg - ref_dg) / abs(ref_dg))
+    assert abs(dg - ref_dg) <= 1e-4 * abs(ref_dg)
+
+
+# ------------------------------------------------------------------------------ edge cases
+def test_degenerate_grids(npb, ctx, O):
+    # n = 3 along every axis: one interior node, one atom exactly on it
+    p = I.Problem(xyz=np.array([[0.5, 0.5, 0.5]]), q=np.array([1.0]), radius=np.array([0.6]), eps_in=1.0,
+                  eps_out=80.0, kappa2=0.84, h=0.5, n=(3, 3, 3), origin=(0.0, 0.0, 0.0))
+    # the stencil of an atom on node 1 reaches node 2 (a face) -> rejected
+    with pytest.raises(npb.NpbError) as e:
+        npb.npb_grid_create(ctx, p)
+    assert e.value.code == npb.NPB_EINVAL
+    # no atoms at all: every potential stays zero and dG = 0
+    p0 = I.Problem(xyz=np.zeros((0, 3)), q=np.zeros(0), radius=np.zeros(0), eps_in=1.0, eps_out=80.0,
+                   kappa2=0.84, h=0.5, n=(5, 4, 3), origin=(0.0, 0.0, 0.0))
+    g = npb.npb_grid_create(ctx, p0)
+    try:
+        assert npb.npb_energy(g, npb.make_opts(0.4, 0.04, 3)) == 0.0
+        assert not npb.npb_potential(g, 0, npb.grid_shape(p0)).any()
+    finally:
+        npb.npb_grid_destroy(g)
+    # longest supported line (288 nodes) against the oracle
+    pl = I.Problem(xyz=np.array([[70.0, 2.0, 2.5]]), q=np.array([0.5]), radius=np.array([1.7]), eps_in=1.0,
+                   eps_out=80.0, kappa2=0.84, h=0.5, n=(288, 9, 11), origin=(0.0, 0.0, 0.0))
+    _energy_case(npb, ctx, O, pl, 0.4, 0.04, 5)
+
+
+def test_invalid_arguments(npb, ctx):
+    p = I.born_sphere(0.0)
+    bad = I.Problem(xyz=p.xyz, q=p.q, radius=p.radius, eps_in=1.0, eps_out=80.0, kappa2=0.0, h=0.5,
+                    n=(289, 33, 33), origin=p.origin)
+    with pytest.raises(npb.NpbError) as e:
+        npb.npb_grid_create(ctx, bad)
+    assert e.value.code == npb.NPB_EINVAL
+    g = npb.npb_grid_create(ctx, p)
+    try:
+        for o in [npb.make_opts(-0.1, 1.0, 5), npb.make_opts(0.1, 0.0, 5), npb.make_opts(0.1, 1.0, 5, scheme=7),
+                  npb.make_opts(0.1, 1.0, 5, vacuum_recovery=False)]:
+            with pytest.raises(npb.NpbError) as e:
+                npb.npb_energy(g, o)
+            assert e.value.code == npb.NPB_EINVAL
+        with pytest.raises(npb.NpbError):
+            npb.npb_lod_solve(g, npb.make_opts(0.1, 1.0, 5), 0, 0.3)
+    finally:
+        npb.npb_grid_destroy(g)
+
+
+def test_graph_replay_is_bitwise_stable(npb, ctx):
+    """The captured graph and the eager (profiled) launch sequence give identical energies."""
+    p = I.random_walk_molecule(200, 65, 0.5, seed=I.SEED_BASE + 71)
+    g = npb.npb_grid_create(ctx, p)
+    try:
+        for prec in (0, 1):
+            o = npb.make_opts(0.4, 0.04, 25, precision=prec)
+            a = npb.npb_energy(g, o)
+            b = npb.npb_energy(g, o)
+            npb.npb_ctx_profile(ctx, True)
+            c = npb.npb_energy(g, o)
+            npb.npb_ctx_profile(ctx, False)
+            assert a == b == c
+    finally:
+        npb.npb_grid_destroy(g)
