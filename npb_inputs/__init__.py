@@ -18,10 +18,42 @@ same seed gives the same molecule on every machine and numpy version.
 """
 from __future__ import annotations
 
+import ctypes
 import math
+import os
+import subprocess
 from dataclasses import dataclass, field
 
 import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_WALK_SRC = os.path.join(_HERE, "walk.c")
+_WALK_LIB = os.path.join(_HERE, "_build", "libwalk.so")
+_walk = None
+
+
+def build_walk() -> str:
+    """Compile walk.c (the random-walk placement) with gcc into npb_inputs/_build."""
+    os.makedirs(os.path.dirname(_WALK_LIB), exist_ok=True)
+    if os.path.exists(_WALK_LIB) and os.path.getmtime(_WALK_LIB) >= os.path.getmtime(_WALK_SRC):
+        return _WALK_LIB
+    tmp = _WALK_LIB + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-o", tmp,
+                           _WALK_SRC, "-lm"])
+    os.replace(tmp, _WALK_LIB)
+    return _WALK_LIB
+
+
+def _walk_lib():
+    global _walk
+    if _walk is None:
+        lib = ctypes.CDLL(build_walk())
+        lib.rw_place.restype = ctypes.c_int
+        lib.rw_place.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                 ctypes.POINTER(ctypes.c_uint64), ctypes.c_double, ctypes.c_double,
+                                 ctypes.c_int, ctypes.c_long, ctypes.POINTER(ctypes.c_double)]
+        _walk = lib
+    return _walk
 
 _MASK64 = (1 << 64) - 1
 
@@ -123,58 +155,22 @@ def born_sphere(kappa2: float = 0.0, n: int = 33, h: float = 0.5, radius: float 
 def random_walk_positions(n_atoms: int, lo: float, hi: float, rng: Xoshiro256ss,
                           step: float = 3.8, min_sep: float = 3.0,
                           max_reject: int = 100) -> np.ndarray:
-    """Confined self-avoiding random walk with branching restarts.
+    """Confined self-avoiding random walk with branching restarts (walk.c).
 
     Each new atom is one `step` from the current atom in a direction uniform on
     the sphere; it is rejected if it leaves the cube [lo, hi]^3 or comes closer
     than `min_sep` to any placed atom.  After `max_reject` consecutive
-    rejections the walk restarts from a uniformly chosen placed atom.
+    rejections the walk restarts from a uniformly chosen placed atom.  The
+    generator `rng` advances exactly as many draws as the walk consumed.
     """
-    cell = min_sep
-    ncell = max(1, int(math.floor((hi - lo) / cell)))
-    grid: dict[tuple[int, int, int], list[int]] = {}
     pos = np.zeros((n_atoms, 3))
-
-    def key(p):
-        return tuple(min(ncell - 1, max(0, int((p[d] - lo) / cell))) for d in range(3))
-
-    def clashes(p):
-        kx, ky, kz = key(p)
-        for dx in (-1, 0, 1):
-            for dy in (-1, 0, 1):
-                for dz in (-1, 0, 1):
-                    for idx in grid.get((kx + dx, ky + dy, kz + dz), ()):
-                        d = pos[idx] - p
-                        if d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < min_sep * min_sep:
-                            return True
-        return False
-
+    state = (ctypes.c_uint64 * 4)(*rng.s)
     budget = 400 * n_atoms + 10000  # total rejections allowed before giving up
-    first = np.array([rng.uniform(lo, hi) for _ in range(3)])
-    pos[0] = first
-    grid.setdefault(key(first), []).append(0)
-    cur = 0
-    placed = 1
-    rejects = 0
-    while placed < n_atoms:
-        cz = rng.uniform(-1.0, 1.0)
-        phi = rng.uniform(0.0, 2.0 * math.pi)
-        sz = math.sqrt(max(0.0, 1.0 - cz * cz))
-        cand = pos[cur] + step * np.array([sz * math.cos(phi), sz * math.sin(phi), cz])
-        if (cand < lo).any() or (cand > hi).any() or clashes(cand):
-            rejects += 1
-            budget -= 1
-            if budget <= 0:
-                raise RuntimeError(f"random walk jammed after {placed} of {n_atoms} atoms")
-            if rejects >= max_reject:
-                cur = rng.below(placed)
-                rejects = 0
-            continue
-        pos[placed] = cand
-        grid.setdefault(key(cand), []).append(placed)
-        cur = placed
-        placed += 1
-        rejects = 0
+    placed = _walk_lib().rw_place(n_atoms, lo, hi, state, step, min_sep, max_reject, budget,
+                                  pos.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    rng.s = [int(x) for x in state]
+    if placed < n_atoms:
+        raise RuntimeError(f"random walk jammed after {placed} of {n_atoms} atoms")
     return pos
 
 

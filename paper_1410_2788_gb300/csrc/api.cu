@@ -401,15 +401,9 @@ int npb::grid_setup(npb_grid *g, cudaStream_t st) {
     CU(setup_charges(g->geo, g->d_xyz, g->d_q, na, g->sc, g->d_line_begin, g->d_line_count, g->d_ent_x,
                      g->d_ent_qt, g->d_ent_off, st));
     if ((rc = pr.end(st, ev, K_SETUP_CHARGES))) return rc;
+    // face data are recomputed on their next use, only for the precision that uses them
     for (int m = 0; m < 2; ++m)
-        for (int k = 0; k < 2; ++k) {
-            if (!g->d_bc[m][k]) continue;
-            const double eps = m == NPB_SOLVENT ? g->eps_out : g->eps_in;
-            const double kbar = m == NPB_SOLVENT ? std::sqrt(g->kappa2) : 0.0;
-            if ((rc = pr.begin(st, &ev))) return rc;
-            CU(setup_boundary(g->geo, g->d_xyz, g->d_q, na, eps, kbar, k == 1, g->d_bc[m][k], st));
-            if ((rc = pr.end(st, ev, K_SETUP_BOUNDARY))) return rc;
-        }
+        for (int k = 0; k < 2; ++k) g->bc_valid[m][k] = false;
     return 0;
 }
 
@@ -431,10 +425,13 @@ extern "C" void npb_grid_destroy(npb_grid *g) { grid_free(g); }
 int npb::grid_boundary(npb_grid *g, int medium, int prec, cudaStream_t st, const double **out) {
     const int kind = prec == NPB_FP64 ? 0 : 1;
     double *&bc = g->d_bc[medium][kind];
-    if (!bc) {
-        const int64_t nf = face_count(g->geo.nx, g->geo.ny, g->geo.nz);
-        int rc = galloc(g, &bc, (size_t)nf);
-        if (rc) return rc;
+    if (!bc || !g->bc_valid[medium][kind]) {
+        int rc;
+        if (!bc) {
+            const int64_t nf = face_count(g->geo.nx, g->geo.ny, g->geo.nz);
+            if ((rc = galloc(g, &bc, (size_t)nf))) return rc;
+        }
+        g->bc_valid[medium][kind] = true;
         const double eps = medium == NPB_SOLVENT ? g->eps_out : g->eps_in;
         const double kbar = medium == NPB_SOLVENT ? std::sqrt(g->kappa2) : 0.0;
         cudaEvent_t ev{};

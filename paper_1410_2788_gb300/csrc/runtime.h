@@ -96,6 +96,7 @@ struct npb_grid {
     int64_t *d_ent_off = nullptr;
     int n_ent = 0;
     double *d_bc[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [medium][0 fp64 | 1 fp32 pairs]
+    bool bc_valid[2][2] = {{false, false}, {false, false}};
     void *d_u[2][4] = {};              // leg states by [precision][slot]
     int u_prec = -1;                   // precision of the last solve (for npb_potential)
     npb::LegDev *d_legs[2] = {};       // device leg tables by precision

@@ -232,10 +232,18 @@ __global__ void k_boundary_f64(GridGeom g, const double *__restrict__ xyz, const
         }
         __syncthreads();
         const int na = min(kAtomChunk, n_atoms - a0);
-        for (int t = 0; t < na; ++t) {
-            const double dx = x - sa[t][0], dy = y - sa[t][1], dz = z - sa[t][2];
-            const double d = sqrt(dx * dx + dy * dy + dz * dz);
-            s += sa[t][3] * exp(-ks * d) / (eps * d);
+        if (ks == 0.0) {  // Coulomb faces: exp(0) = 1 exactly, so the sum is unchanged
+            for (int t = 0; t < na; ++t) {
+                const double dx = x - sa[t][0], dy = y - sa[t][1], dz = z - sa[t][2];
+                const double d = sqrt(dx * dx + dy * dy + dz * dz);
+                s += sa[t][3] / (eps * d);
+            }
+        } else {
+            for (int t = 0; t < na; ++t) {
+                const double dx = x - sa[t][0], dy = y - sa[t][1], dz = z - sa[t][2];
+                const double d = sqrt(dx * dx + dy * dy + dz * dz);
+                s += sa[t][3] * exp(-ks * d) / (eps * d);
+            }
         }
     }
     if (f < nf) out[f] = kBjerrum * s;
