@@ -47,25 +47,30 @@ __device__ __forceinline__ double fast_rcp<double>(double x) {
     return 1.0 / x;
 }
 
-__device__ __forceinline__ float t_expm1(float x) { return expm1f(x); }
-__device__ __forceinline__ double t_expm1(double x) { return expm1(x); }
-__device__ __forceinline__ float t_log1p(float x) { return log1pf(x); }
-__device__ __forceinline__ double t_log1p(double x) { return log1p(x); }
-
 // The nonlinear stage of Eq. (ana3) in tanh form: tanh(w'/2) = q tanh(w/2), q =
 // exp(-kbar^2 tau).  With e = exp(-|w|), tanh(|w|/2) = (1-e)/(1+e) and
 // 1 - tanh(|w'|/2) = (1-q) + 2 q e/(1+e); then |w'| = log1p(2 t'/(1 - t')).  No term
 // overflows for any w and no step subtracts nearly equal numbers.
-template <typename T>
-__device__ __forceinline__ T nl_flow(T w, T q, T omq) {
-    const T aw = fabs(w);
-    const T em = t_expm1(-aw);  // e - 1
-    const T e = em + T(1);
-    const T inv = T(1) / (T(1) + e);
-    const T t = -q * em * inv;
-    const T omt = omq + T(2) * q * e * inv;
-    const T wn = t_log1p(T(2) * t / omt);
-    return copysign(wn, w);
+__device__ __forceinline__ double nl_flow(double w, double q, double omq) {
+    const double aw = fabs(w);
+    const double em = expm1(-aw);  // e - 1
+    const double e = em + 1.0;
+    const double inv = 1.0 / (1.0 + e);
+    const double t = -q * em * inv;
+    const double omt = omq + 2.0 * q * e * inv;
+    return copysign(log1p(2.0 * t / omt), w);
+}
+
+// FP32 flavour on the special-function unit: the absolute error of w' stays at a few
+// 1e-7 for every w (relative error is larger only where |w'| itself is below ~1e-3),
+// well inside the mixed path's stated tolerance.
+__device__ __forceinline__ float nl_flow(float w, float q, float omq) {
+    const float aw = fabsf(w);
+    const float e = __expf(-aw);
+    const float inv = fast_rcp(1.0f + e);
+    const float t = q * (1.0f - e) * inv;
+    const float omt = omq + 2.0f * q * e * inv;
+    return copysignf(__logf(1.0f + 2.0f * t * fast_rcp(omt)), w);
 }
 
 template <typename T>
