@@ -184,6 +184,35 @@ int npb_apply(npb_grid *grid, const npb_opts *opts, int32_t leg, int32_t op, dou
  * stated type and n_elems must equal nx*ny*nz. */
 int npb_grid_export(npb_grid *grid, int32_t what, void *host_out, size_t n_elems);
 
+/* ---- charge list without allocation --------------------------------------------------- */
+/* The paper has no counterpart: this is a service for callers that cannot allocate device
+ * memory when they need a charge list -- code in the middle of capturing a CUDA graph,
+ * applications whose own memory pool owns the device and forbids library allocations, and
+ * latency-critical paths that cannot pay for cudaMalloc's implicit synchronisation.
+ *
+ * It builds the same x-line-grouped trilinear charge list as npb_grid_create, on the calling
+ * thread's current device and on `stream` (a cudaStream_t; NULL = the legacy default
+ * stream), and calls no cudaMalloc, cudaFree or allocating routine.  Its temporaries live in
+ * one fixed device array compiled into the library (about 9.3 MB on every GPU that loads it,
+ * kept until the process exits), which bounds the problem: n_atoms <= NPB_STATIC_MAX_ATOMS
+ * and ny*nz <= NPB_STATIC_MAX_LINES; larger inputs return NPB_EINVAL.  The first call on a
+ * device looks the array up (cudaGetSymbolAddress) -- make it before any stream capture.
+ * Every call reuses the same array: calls that overlap on the GPU race, so serialise them.
+ *
+ * Inputs (host memory): xyz (3*n_atoms doubles), q (n_atoms), grid n, h, origin as in
+ * npb_problem; every atom's 8-node stencil must lie in the interior.  Outputs (device memory
+ * the caller owns): d_line_begin and d_line_count (ny*nz each; entries of x-line z*ny + y),
+ * d_ent_x, d_ent_qt and d_ent_off (room for 8*n_atoms each: node x index, charge in e_c,
+ * element offset (z*ny + y)*pitch + x with pitch = nx rounded up to 32), and d_n_entries
+ * (one int32: the number of entries).  The work is enqueued; synchronise `stream` before
+ * reading the outputs. */
+#define NPB_STATIC_MAX_ATOMS 20000
+#define NPB_STATIC_MAX_LINES (288 * 288)
+int npb_charge_list_static(const double *xyz, const double *q, int32_t n_atoms, const int32_t n[3], double h,
+                           const double origin[3], int32_t *d_line_begin, int32_t *d_line_count,
+                           int32_t *d_ent_x, double *d_ent_qt, int64_t *d_ent_off, int32_t *d_n_entries,
+                           void *stream);
+
 /* ---- serving: continuous batching ---------------------------------------------------- */
 /* Queue one RE+V energy request; the library copies the problem.  A scheduler thread
  * admits queued requests while their device footprint fits the budget, runs the legs

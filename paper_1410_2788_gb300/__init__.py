@@ -90,6 +90,8 @@ SIGNATURES = {
     "npb_tune_set": (_I, [_V, _I32, _I32, _I32, _I32, _I32, _I32]),
     "npb_tune_get": (_I, [_V, _I32, _I32, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32),
                           ctypes.POINTER(_I32)]),
+    "npb_charge_list_static": (_I, [_dp, _dp, _I32, ctypes.POINTER(_I32), ctypes.c_double, _dp, _V, _V, _V, _V,
+                                    _V, _V, _V]),
     "npb_last_error": (ctypes.c_char_p, []),
     "npb_version": (ctypes.c_char_p, []),
 }
@@ -262,6 +264,21 @@ def npb_tune_get(ctx: int, precision: int, direction: int, n: int) -> tuple[int,
     _check(load_library().npb_tune_get(ctx, precision, direction, n, ctypes.byref(a), ctypes.byref(b),
                                        ctypes.byref(c)))
     return a.value, b.value, c.value
+
+
+NPB_STATIC_MAX_ATOMS = 20000
+NPB_STATIC_MAX_LINES = 288 * 288
+
+
+def npb_charge_list_static(problem, d_line_begin: int, d_line_count: int, d_ent_x: int, d_ent_qt: int,
+                           d_ent_off: int, d_n_entries: int, stream: int | None = None) -> None:
+    """Charge list into caller-owned device buffers (raw device pointers), with no allocation."""
+    arr = _Arrays(problem)
+    n = (_I32 * 3)(*[int(v) for v in problem.n])
+    org = (ctypes.c_double * 3)(*[float(v) for v in problem.origin])
+    _check(load_library().npb_charge_list_static(
+        arr.xyz.ctypes.data_as(_dp), arr.q.ctypes.data_as(_dp), arr.struct.n_atoms, n, float(problem.h), org,
+        d_line_begin, d_line_count, d_ent_x, d_ent_qt, d_ent_off, d_n_entries, stream or None))
 
 
 def npb_last_error() -> str:
