@@ -19,6 +19,7 @@
 #include "npb_internal.cuh"
 #include "runtime.h"
 #include "setup_kernels.cuh"
+#include "sweep_tma.cuh"
 
 using namespace npb;
 
@@ -180,6 +181,7 @@ extern "C" int npb_ctx_create(int device, size_t budget, npb_ctx **out) {
     ctx->stream = ctx->own_stream;
     CU(prepare_sweep_f32());
     CU(prepare_sweep_f64());
+    CU(prepare_sweep_tma());
     *out = ctx.release();
     return NPB_OK;
 }
@@ -283,7 +285,7 @@ extern "C" size_t npb_grid_footprint(const npb_problem *p, int32_t precision) {
     const size_t na = p->n_atoms > 0 ? p->n_atoms : 0;
     size_t b = 0;
     b += 4 * state_bytes(p->n, precision);                       // four leg states
-    b += (pitch / 32) * lines * 4;                                // node mask
+    b += (size_t)mask_words_per_row((int)pitch) * lines * 4;     // node mask
     b += 2 * lines * 4 + 8 * na * (4 + 8 + 8);                    // charge list
     b += 4 * (size_t)face_count(p->n[0], p->n[1], p->n[2]) * 8;  // face data, 2 media x 2 kinds
     b += na * 5 * 8 + 4096;                                       // atoms, result slot
@@ -334,7 +336,7 @@ int npb::grid_build(npb_ctx *ctx, const npb_problem *p, cudaStream_t st, npb_gri
     g->n_atoms = p->n_atoms;
     const int na = p->n_atoms;
     const int n_lines = g->geo.ny * g->geo.nz;
-    const size_t words = (size_t)(g->geo.pitch / 32) * n_lines;
+    const size_t words = (size_t)mask_words_per_row(g->geo.pitch) * n_lines;
     auto guard = [&](int r) {
         if (r) grid_free(g);
         return r;
@@ -350,6 +352,8 @@ int npb::grid_build(npb_ctx *ctx, const npb_problem *p, cudaStream_t st, npb_gri
     if ((rc = galloc(g, &g->d_ent_qt, n_raw))) return guard(rc);
     if ((rc = galloc(g, &g->d_ent_off, n_raw))) return guard(rc);
     if ((rc = galloc(g, &g->d_result, 8))) return guard(rc);
+    if ((rc = galloc(g, &g->d_err, 4))) return guard(rc);
+    CU(cudaMemsetAsync(g->d_err, 0, 4 * sizeof(int32_t), st));
     if (cudaMallocHost(&g->h_result, 8 * sizeof(double)) != cudaSuccess) {
         g->h_result = nullptr;
         return guard(fail(NPB_ENOMEM, "cudaMallocHost failed"));
@@ -388,7 +392,7 @@ int npb::grid_build(npb_ctx *ctx, const npb_problem *p, cudaStream_t st, npb_gri
 int npb::grid_setup(npb_grid *g, cudaStream_t st) {
     Profiler &pr = g->ctx->prof;
     const int na = g->n_atoms;
-    const size_t words = (size_t)(g->geo.pitch / 32) * g->geo.ny * g->geo.nz;
+    const size_t words = (size_t)mask_words_per_row(g->geo.pitch) * g->geo.ny * g->geo.nz;
     int rc;
     cudaEvent_t ev{};
     CU(cudaMemsetAsync(g->d_mask, 0, words * 4, st));
@@ -445,7 +449,7 @@ int npb::grid_boundary(npb_grid *g, int medium, int prec, cudaStream_t st, const
 
 int npb::grid_half_masks(npb_grid *g, cudaStream_t st) {
     if (g->d_half[0]) return 0;
-    const size_t words = (size_t)(g->geo.pitch / 32) * g->geo.ny * g->geo.nz;
+    const size_t words = (size_t)mask_words_per_row(g->geo.pitch) * g->geo.ny * g->geo.nz;
     for (int d = 0; d < 3; ++d) {
         int rc = galloc(g, &g->d_half[d], words);
         if (rc) return rc;
@@ -536,6 +540,7 @@ int npb::grid_prepare(npb_grid *g, const npb_opts *o, cudaStream_t st) {
     int rc = grid_states(g, o->precision, st);
     if (rc) return rc;
     if (o->eps_mode == NPB_EPS_MIDPOINT && (rc = grid_half_masks(g, st))) return rc;
+    if (o->precision == NPB_FP32_SWEEP && (rc = grid_tma(g))) return rc;
     const int prec = o->precision;
     g->u_prec = prec;
     char key[256];
@@ -549,33 +554,98 @@ int npb::grid_prepare(npb_grid *g, const npb_opts *o, cudaStream_t st) {
 }
 
 SweepShape npb::shape_for(npb_ctx *ctx, int prec, int dir, int n) {
-    std::lock_guard<std::mutex> lk(ctx->tune_mu);
-    auto it = ctx->tuned.find(tune_key(prec, dir, n));
-    if (it != ctx->tuned.end()) return it->second;
+    {
+        std::lock_guard<std::mutex> lk(ctx->tune_mu);
+        auto it = ctx->tuned.find(tune_key(prec, dir, n));
+        if (it != ctx->tuned.end()) return it->second;
+    }
+    if (prec == NPB_FP32_SWEEP) {  // the TMA pipeline: smallest SEG*L >= n, ties to longer segments
+        SweepShape t[16], best{0, 0, 0, 0};
+        const int k = tma_shapes(dir, t, 16);
+        for (int i = 0; i < k; ++i) {
+            if (t[i].seg * t[i].len < n) continue;
+            if (best.tx == 0 || t[i].seg * t[i].len < best.seg * best.len ||
+                (t[i].seg * t[i].len == best.seg * best.len && t[i].len > best.len))
+                best = t[i];
+        }
+        if (best.tx) return best;
+    }
     return default_sweep_shape(prec, dir, n);
 }
 
-// One LOD step for legs [slot0, slot0 + n_legs) of the device table.
+// Tensor maps of the FP32 leg states and of the mask, built once per grid.
+int npb::grid_tma(npb_grid *g) {
+    if (g->tma_built) return 0;
+    g->tma_built = true;
+    const int nx = g->geo.nx, ny = g->geo.ny, nz = g->geo.nz, pitch = g->geo.pitch;
+    for (int d = 0; d < 3; ++d) {
+        g->tma_g[d] = tma_geometry(d, nx, ny, nz, pitch);
+        bool ok = g->tma_g[d].ok && g->d_u[NPB_FP32_SWEEP][0] != nullptr;
+        for (int s = 0; s < 4 && ok; ++s)
+            ok = tma_encode_state(&g->tma_u[d][s], g->d_u[NPB_FP32_SWEEP][s], d, g->tma_g[d], nx, ny, nz, pitch);
+        if (ok) ok = tma_encode_mask(&g->tma_m[d], g->d_mask, d, g->tma_g[d], ny, nz);
+        g->tma_ok[d] = ok;
+    }
+    return 0;
+}
+
+// One sweep direction over legs [slot0, slot0 + n_legs): the TMA pipeline for FP32 when
+// the shape asks for it and the grid's geometry allows it, else the one-tile-per-block kernel.
+cudaError_t npb::launch_dir(npb_grid *g, int prec, int d, SweepShape shape, int slot0, int n_legs, int flags,
+                            cudaStream_t st) {
+    const int nx = g->geo.nx, ny = g->geo.ny, nz = g->geo.nz;
+    const int n_dir[3] = {nx, ny, nz};
+    // the TMA kernels take eps at half points from the node mask (harmonic reading only)
+    if (shape.kind == 1 && prec == NPB_FP32_SWEEP && g->tma_ok[d] && n_legs <= kTmaMaxLegs &&
+        g->h_legs[prec][slot0].eps_mode == 0) {
+        TmaLaunch P;
+        memset(&P, 0, sizeof P);
+        for (int i = 0; i < n_legs; ++i) {
+            P.umap[i] = g->tma_u[d][slot0 + i];
+            P.mmap[i] = g->tma_m[d];
+            P.legs[i] = g->h_legs[prec][slot0 + i];
+        }
+        P.n_legs = n_legs;
+        P.err = g->d_err;
+        return launch_sweep_tma(d, P, g->tma_g[d], flags, shape, g->ctx->sm_count, st);
+    }
+    if (shape.kind == 1) shape = default_sweep_shape(prec, d, n_dir[d]);
+    return launch_sweep(prec, d, g->d_legs[prec] + slot0, n_legs, nx, ny, nz, flags, shape, st);
+}
+
+// One LOD step for legs [slot0, slot0 + n_legs) of the leg table.  FP32 legs use the
+// TMA-pipelined sweeps where the grid's geometry allows it (the source stage then runs as its
+// own sparse launch); otherwise the one-tile-per-block sweeps with the source fused into x.
 int npb::run_step(npb_grid *g, int prec, int scheme, int slot0, int n_legs, cudaStream_t st) {
     Profiler &pr = g->ctx->prof;
     const LegDev *legs = g->d_legs[prec] + slot0;
     const int nx = g->geo.nx, ny = g->geo.ny, nz = g->geo.nz;
     const int n_dir[3] = {nx, ny, nz};
+    SweepShape shape[3];
+    bool tma[3];
+    for (int d = 0; d < 3; ++d) {
+        shape[d] = shape_for(g->ctx, prec, d, n_dir[d]);
+        tma[d] = shape[d].kind == 1 && prec == NPB_FP32_SWEEP && g->tma_ok[d] && n_legs <= kTmaMaxLegs &&
+                 g->h_legs[prec][slot0].eps_mode == 0;
+        if (shape[d].kind == 1 && !tma[d]) shape[d] = default_sweep_shape(prec, d, n_dir[d]);
+    }
+    cudaEvent_t ev{};
+    int rc;
+    if (scheme == NPB_LODIE2 && tma[0]) {
+        if ((rc = pr.begin(st, &ev))) return rc;
+        CU(launch_source(prec, legs, n_legs, ny, nz, st));
+        if ((rc = pr.end(st, ev, K_SOURCE))) return rc;
+    }
     for (int d = 0; d < 3; ++d) {
         int flags = 0;
-        if (d == 0) flags = scheme == NPB_LODIE2 ? FUSE_PRE_SRC : FUSE_PRE_NL;
+        if (d == 0) flags = scheme == NPB_LODIE2 ? (tma[0] ? 0 : FUSE_PRE_SRC) : FUSE_PRE_NL;
         if (d == 2 && scheme == NPB_LODIE2) flags = FUSE_POST_NL;
-        const SweepShape s = shape_for(g->ctx, prec, d, n_dir[d]);
-        cudaEvent_t ev{};
-        int rc = pr.begin(st, &ev);
-        if (rc) return rc;
-        CU(launch_sweep(prec, d, legs, n_legs, nx, ny, nz, flags, s, st));
+        if ((rc = pr.begin(st, &ev))) return rc;
+        CU(launch_dir(g, prec, d, shape[d], slot0, n_legs, flags, st));
         if ((rc = pr.end(st, ev, K_SWEEP_X + d))) return rc;
     }
     if (scheme == NPB_LODIE1) {
-        cudaEvent_t ev{};
-        int rc = pr.begin(st, &ev);
-        if (rc) return rc;
+        if ((rc = pr.begin(st, &ev))) return rc;
         CU(launch_source(prec, legs, n_legs, ny, nz, st));
         if ((rc = pr.end(st, ev, K_SOURCE))) return rc;
     }
@@ -624,6 +694,25 @@ int npb::enqueue_energy(npb_grid *g, const npb_opts *o, cudaStream_t st) {
                      g->d_ent_off, g->d_ent_qt, g->sc.total, re, g->d_result, st));
     if ((rc = g->ctx->prof.end(st, ev, K_ENERGY))) return rc;
     CU(cudaMemcpyAsync(g->h_result, g->d_result, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(reinterpret_cast<int32_t *>(g->h_result + 1), g->d_err, sizeof(int32_t),
+                       cudaMemcpyDeviceToHost, st));
+    return 0;
+}
+
+// A device wait that expired leaves its flag set: report it, then clear it.
+int npb::grid_check_err(npb_grid *g, cudaStream_t st, int host_copy) {
+    int32_t e = 0;
+    if (host_copy) {
+        e = *reinterpret_cast<int32_t *>(g->h_result + 1);
+    } else {
+        CU(cudaMemcpyAsync(&e, g->d_err, sizeof e, cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+    }
+    if (e) {
+        CU(cudaMemsetAsync(g->d_err, 0, sizeof(int32_t), st));
+        CU(cudaStreamSynchronize(st));
+        return fail(NPB_ETIMEOUT, "a bounded device wait expired in a sweep (tile copies did not complete)");
+    }
     return 0;
 }
 
@@ -675,6 +764,7 @@ extern "C" int npb_energy(npb_grid *g, const npb_opts *o, double *dG) {
         if ((rc = enqueue_energy(g, o, st))) return rc;
     }
     CU(cudaStreamSynchronize(st));
+    if ((rc = grid_check_err(g, st, 1))) return rc;
     *dG = g->h_result[0];
     return NPB_OK;
 }
@@ -695,7 +785,7 @@ extern "C" int npb_lod_solve(npb_grid *g, const npb_opts *o, int32_t medium, dou
     for (int s = 0; s < steps; ++s)
         if ((rc = run_step(g, o->precision, o->scheme, kLegSlot[leg], 1, st))) return rc;
     CU(cudaStreamSynchronize(st));
-    return NPB_OK;
+    return grid_check_err(g, st, 0);
 }
 
 extern "C" int npb_potential(npb_grid *g, int32_t leg, double *host_out, size_t n_elems) {
@@ -748,7 +838,7 @@ extern "C" int npb_apply(npb_grid *g, const npb_opts *o, int32_t leg, int32_t op
         case NPB_OP_SWEEP_Y:
         case NPB_OP_SWEEP_Z: {
             const int d = op - NPB_OP_SWEEP_X;
-            e = launch_sweep(prec, d, legs, 1, nx, ny, nz, 0, shape_for(g->ctx, prec, d, n_dir[d]), st);
+            e = launch_dir(g, prec, d, shape_for(g->ctx, prec, d, n_dir[d]), slot, 1, 0, st);
             break;
         }
         case NPB_OP_STEP: {
@@ -767,7 +857,7 @@ extern "C" int npb_apply(npb_grid *g, const npb_opts *o, int32_t leg, int32_t op
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     g->ctx->release(tmp, total * sizeof(double));
     if (e != cudaSuccess) return fail(NPB_ECUDA, "npb_apply failed: %s", cudaGetErrorString(e));
-    return NPB_OK;
+    return grid_check_err(g, st, 0);
 }
 
 extern "C" int npb_grid_export(npb_grid *g, int32_t what, void *host_out, size_t n_elems) {

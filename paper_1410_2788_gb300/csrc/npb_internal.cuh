@@ -5,7 +5,8 @@
 //           every x-row starts on a 128-byte boundary.  Faces (an index 0 or n-1)
 //           hold the Dirichlet data and are never written by a sweep; padding
 //           columns x >= nx are zero.
-//   mask  : uint32[nz][ny][pitch/32]; bit x of row (y, z) is 1 on/inside the
+//   mask  : uint32[nz][ny][mwpr], mwpr = pitch/32 rounded up to 4 words (16-byte rows, so
+//           the mask can be a TMA tensor); bit x of row (y, z) is 1 on/inside the
 //           molecule (Omega_m).  Vacuum legs pass no mask (every node "inside").
 //   half  : for NPB_EPS_MIDPOINT, one such bit array per direction d, whose bit at
 //           node p says that the half point p + e_d/2 is inside.
@@ -24,6 +25,9 @@ constexpr double kBjerrum = kCoulomb / kKT;      // e_c^2 / (k_B T) in A
 constexpr double kPi = 3.14159265358979323846;
 
 enum Dir { DIR_X = 0, DIR_Y = 1, DIR_Z = 2 };
+
+// uint32 words per x-row of a bit array: pitch/32 rounded up to a multiple of 4.
+__host__ __device__ __forceinline__ int mask_words_per_row(int pitch) { return ((pitch >> 5) + 3) & ~3; }
 
 // Everything a sweep / stage kernel needs for one leg.  Lives in device memory as an
 // array indexed by blockIdx.z, so one launch can advance several legs of equal size.
@@ -53,6 +57,7 @@ enum : int {
 
 struct SweepShape {     // one instantiated line-solver shape
     int tx, seg, len;
+    int kind;           // 0: one tile per block, direct loads; 1: persistent TMA pipeline (FP32)
 };
 
 // Launchers (defined in sweep_*.cu).  Return cudaError of the launch.

@@ -15,6 +15,7 @@
 #include "../../include/npb.h"
 #include "npb_internal.cuh"
 #include "setup_kernels.cuh"
+#include "tma.h"
 
 namespace npb {
 
@@ -104,6 +105,12 @@ struct npb_grid {
     std::string legs_key[2];
     double *d_result = nullptr;
     double *h_result = nullptr;  // pinned
+    int32_t *d_err = nullptr;    // set by a device wait that expired
+    CUtensorMap tma_u[3][4];     // FP32 leg states by [direction][slot]
+    CUtensorMap tma_m[3];        // node mask by direction
+    npb::TmaGeom tma_g[3] = {};
+    bool tma_ok[3] = {false, false, false};
+    bool tma_built = false;
     void *d_scratch = nullptr;   // charge-list scratch (kept for re-running set-up)
     size_t scratch_bytes = 0;
     npb::ChargeScratch sc{};
@@ -126,6 +133,9 @@ int grid_prepare(Grid *g, const npb_opts *o, cudaStream_t st);
 LegDev make_leg(const Grid *g, int leg, const npb_opts *o);
 SweepShape shape_for(Ctx *ctx, int prec, int dir, int n);
 int run_step(Grid *g, int prec, int scheme, int slot0, int n_legs, cudaStream_t st);
+int grid_tma(Grid *g);
+cudaError_t launch_dir(Grid *g, int prec, int d, SweepShape shape, int slot0, int n_legs, int flags, cudaStream_t st);
+int grid_check_err(Grid *g, cudaStream_t st, int host_copy);
 int init_legs(Grid *g, int prec, const int *legs, int n, cudaStream_t st);
 int enqueue_energy(Grid *g, const npb_opts *o, cudaStream_t st);
 void serve_shutdown(Ctx *ctx);

@@ -48,7 +48,7 @@ __global__ void k_mask_atoms(GridGeom g, const double *__restrict__ xyz,
     const int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1, ez = hi[2] - lo[2] + 1;
     if (ex <= 0 || ey <= 0 || ez <= 0) return;
     const int total = ex * ey * ez;
-    const int wpr = g.pitch >> 5;
+    const int wpr = mask_words_per_row(g.pitch);
     const double hh = __dmul_rn(0.5, g.h);
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
         const int i = lo[0] + t % ex;
@@ -335,7 +335,7 @@ __global__ void k_pad(GridGeom g, const double *__restrict__ in, T *__restrict__
 
 __global__ void k_mask_dense(GridGeom g, const uint32_t *__restrict__ mask, uint8_t *__restrict__ out) {
     const int64_t total = (int64_t)g.nz * g.ny * g.nx;
-    const int wpr = g.pitch >> 5;
+    const int wpr = mask_words_per_row(g.pitch);
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
          p += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(p % g.nx);

@@ -17,7 +17,7 @@ __global__ void k_nonlinear(const LegDev *__restrict__ legs) {
     const LegDev *lg = legs + blockIdx.z;
     if (!lg->nl_on) return;
     T *u = static_cast<T *>(lg->u);
-    const int nx = lg->nx, ny = lg->ny, nz = lg->nz, pitch = lg->pitch, wpr = pitch >> 5;
+    const int nx = lg->nx, ny = lg->ny, nz = lg->nz, pitch = lg->pitch, wpr = mask_words_per_row(pitch);
     const int64_t total = (int64_t)(nz - 2) * (ny - 2) * (nx - 2);
     const T q = (T)lg->nl_q, omq = (T)lg->nl_omq;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;

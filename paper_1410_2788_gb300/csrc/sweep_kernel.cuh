@@ -86,6 +86,8 @@ struct Vec16<double> {
     static constexpr int n = 2;
 };
 
+constexpr int kMaxLineWords = 288;  // rows of the longest supported line
+
 __host__ __device__ __forceinline__ int sweep_tile_stride(int nx, int vec) {
     const int nxv = (nx + vec - 1) / vec * vec;
     return nxv | 1;
@@ -98,181 +100,25 @@ __host__ __device__ __forceinline__ size_t sweep_smem_bytes(int nx, int pitch) {
         const int S = sweep_tile_stride(nx, Vec16<T>::n);
         b += (size_t)TX * S * sizeof(T);
         b = (b + 15) & ~(size_t)15;
-        b += (size_t)2 * TX * (pitch / 32) * sizeof(uint32_t);
+        b += (size_t)2 * TX * mask_words_per_row(pitch) * sizeof(uint32_t);
+    } else {
+        b = (b + 15) & ~(size_t)15;
+        b += (size_t)2 * kMaxLineWords * sizeof(uint32_t);  // the block's mask column (+ half bits)
     }
     return b;
 }
 
-template <typename T, int DIR, int TX, int SEG, int L>
-__global__ void __launch_bounds__(TX *SEG)
-    sweep_kernel(const LegDev *__restrict__ legs, int flags) {
-    static_assert(L >= 2 && L <= 62, "segment length");
-    static_assert((SEG & (SEG - 1)) == 0, "SEG must be a power of two");
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-
-    const LegDev *lg = legs + blockIdx.z;
-    const int nx = lg->nx, ny = lg->ny, nz = lg->nz, pitch = lg->pitch;
-    const int wpr = pitch >> 5;
-    const int line = threadIdx.x;
-    const int seg = threadIdx.y;
-    const int g0 = seg * L;
-    T *__restrict__ u = static_cast<T *>(lg->u);
-    const uint32_t *__restrict__ mask = lg->mask;
-    const int mid = lg->eps_mode;
-    const uint32_t *__restrict__ half = lg->half[DIR];
-    const int ndir = DIR == DIR_X ? nx : (DIR == DIR_Y ? ny : nz);
-    const T rE0 = (T)lg->rE[0], rE1 = (T)lg->rE[1], rE2 = (T)lg->rE[2];
-    const T nlq = (T)lg->nl_q, nlomq = (T)lg->nl_omq;
-    const bool nl_on = lg->nl_on != 0;
-
-    // ---- shared memory carve-up
-    T *red = reinterpret_cast<T *>(smem_raw);          // 13 * TX * SEG
-    T *fbuf = red;                                      // [SEG][TX][4]
-    T *pbuf = red + 4 * TX * SEG;                       // [2][SEG][TX][4]
-    T *ebuf = red + 12 * TX * SEG;                      // [SEG][TX]
-    T *tile = red + 13 * TX * SEG;                      // DIR_X: [TX][S]
-    const int S = sweep_tile_stride(nx, Vec16<T>::n);
-    uint32_t *smask = nullptr, *shalf = nullptr;
-    if (DIR == DIR_X) {
-        size_t off = (size_t)13 * TX * SEG * sizeof(T) + (size_t)TX * S * sizeof(T);
-        off = (off + 15) & ~(size_t)15;
-        smask = reinterpret_cast<uint32_t *>(smem_raw + off);
-        shalf = smask + TX * wpr;
-    }
-
-    // ---- this thread's line
-    int lx = 0, ly = 0, lz = 0;
-    bool active;
-    int64_t base, stride;
-    if (DIR == DIR_X) {
-        ly = 1 + blockIdx.x * TX + line;
-        lz = 1 + blockIdx.y;
-        active = ly <= ny - 2;
-        base = ((int64_t)lz * ny + ly) * pitch;
-        stride = 1;
-    } else if (DIR == DIR_Y) {
-        lx = blockIdx.x * TX + line;
-        lz = 1 + blockIdx.y;
-        active = lx >= 1 && lx <= nx - 2;
-        base = (int64_t)lz * ny * pitch + lx;
-        stride = pitch;
-    } else {
-        lx = blockIdx.x * TX + line;
-        ly = 1 + blockIdx.y;
-        active = lx >= 1 && lx <= nx - 2;
-        base = (int64_t)ly * pitch + lx;
-        stride = (int64_t)ny * pitch;
-    }
-
-    // ---- X sweep: stage the TX x-rows (and their mask words) in shared memory
-    if (DIR == DIR_X) {
-        constexpr int VEC = Vec16<T>::n;
-        using V = typename Vec16<T>::type;
-        const int nvec = (nx + VEC - 1) / VEC;
-        const int tid = threadIdx.y * TX + threadIdx.x;
-        const int nthr = TX * SEG;
-        const int y0 = 1 + blockIdx.x * TX;
-        for (int i = tid; i < TX * nvec; i += nthr) {
-            const int l = i / nvec, v = i - l * nvec;
-            const int y = y0 + l;
-            T vals[VEC];
-            if (y <= ny - 2) {
-                const V w = *reinterpret_cast<const V *>(u + ((int64_t)lz * ny + y) * pitch + v * VEC);
-                *reinterpret_cast<V *>(vals) = w;
-            } else {
-#pragma unroll
-                for (int e = 0; e < VEC; ++e) vals[e] = T(0);
-            }
-#pragma unroll
-            for (int e = 0; e < VEC; ++e) tile[l * S + v * VEC + e] = vals[e];
-        }
-        for (int i = tid; i < TX * wpr; i += nthr) {
-            const int l = i / wpr, w = i - l * wpr;
-            const int y = y0 + l;
-            const int64_t row = ((int64_t)lz * ny + (y <= ny - 2 ? y : 0)) * wpr + w;
-            smask[i] = mask ? __ldg(mask + row) : 0xffffffffu;
-            shalf[i] = (mid && half) ? __ldg(half + row) : 0u;
-        }
-        __syncthreads();
-        if (flags & FUSE_PRE_SRC) {
-            const double src = lg->src;
-            for (int l = tid; l < TX; l += nthr) {
-                const int y = y0 + l;
-                if (y > ny - 2) continue;
-                const int ln = lz * ny + y;
-                const int b = lg->line_begin[ln], c = lg->line_count[ln];
-                for (int e = b; e < b + c; ++e)
-                    tile[l * S + lg->ent_x[e]] += (T)(src * lg->ent_qt[e]);
-            }
-            __syncthreads();
-        }
-    }
-
-    // ---- node bits of rows g0-1 .. g0+L (bit k+1 <-> row g0+k), half bits likewise
-    uint64_t nb = 0, hb = 0;
-#pragma unroll
-    for (int k = -1; k <= L; ++k) {
-        const int g = g0 + k;
-        uint32_t bit = 1u, hbit = 0u;
-        if (g >= 0 && g < ndir && active) {
-            if (DIR == DIR_X) {
-                bit = (smask[line * wpr + (g >> 5)] >> (g & 31)) & 1u;
-                if (mid) hbit = (shalf[line * wpr + (g >> 5)] >> (g & 31)) & 1u;
-            } else {
-                const int64_t row = DIR == DIR_Y ? ((int64_t)lz * ny + g) : ((int64_t)g * ny + ly);
-                const int64_t w = row * wpr + (lx >> 5);
-                if (mask) bit = (__ldg(mask + w) >> (lx & 31)) & 1u;
-                if (mid && half) hbit = (__ldg(half + w) >> (lx & 31)) & 1u;
-            }
-        }
-        nb |= (uint64_t)bit << (k + 1);
-        hb |= (uint64_t)hbit << (k + 1);
-    }
-
-    // ---- load the segment's right-hand sides
-    T al[L], be[L], ga[L];
-#pragma unroll
-    for (int k = 0; k < L; ++k) {
-        const int g = g0 + k;
-        T v = T(0);
-        if (active && g < ndir) {
-            if (DIR == DIR_X) v = tile[line * S + g];
-            else v = u[base + (int64_t)g * stride];
-            if ((flags & FUSE_PRE_NL) && nl_on && g >= 1 && g <= ndir - 2 &&
-                ((nb >> (k + 1)) & 1u) == 0u)
-                v = nl_flow(v, nlq, nlomq);
-        }
-        al[k] = v;
-    }
-
-    auto coef = [&](int k, T &a, T &b, T &c) {
-        const int g = g0 + k;
-        if (g < 1 || g > ndir - 2) {
-            a = T(0);
-            b = T(1);
-            c = T(0);
-            return;
-        }
-        T em, ep;
-        if (mid) {
-            em = ((hb >> k) & 1u) ? rE2 : rE0;        // half point g - 1/2
-            ep = ((hb >> (k + 1)) & 1u) ? rE2 : rE0;  // half point g + 1/2
-        } else {
-            const uint32_t bm = (nb >> k) & 1u, b0 = (nb >> (k + 1)) & 1u, bp = (nb >> (k + 2)) & 1u;
-            const uint32_t im = bm + b0, ip = b0 + bp;
-            em = im == 2u ? rE2 : (im == 1u ? rE1 : rE0);
-            ep = ip == 2u ? rE2 : (ip == 1u ? rE1 : rE0);
-        }
-        a = -em;
-        c = -ep;
-        b = T(1) + em + ep;
-    };
-
-    // ---- 1. local modified Thomas
+// Local modified Thomas over the rows strictly inside one segment (rows 1 .. L-2), for
+// row coefficients given by coef(k, a, b, c).  On return, for 1 <= k <= L-2:
+//     x_k = al[k] + be[k] F + ga[k] E,
+// and the segment's first and last rows have become (fa, fb, fc | fd) coupling
+// (E_prev, F, E) and (ea, eb, ec | ed) coupling (F, E, F_next).
+template <typename T, int L, typename Coef>
+__device__ __forceinline__ void segment_reduce(T (&al)[L], T (&be)[L], T (&ga)[L], const Coef &coef, T &fa,
+                                               T &fb, T &fc, T &fd, T &ea, T &eb, T &ec, T &ed) {
     T a0, b0, c0, aL, bL, cL;
     coef(0, a0, b0, c0);
     coef(L - 1, aL, bL, cL);
-    T fa, fb, fc, fd, ea, eb, ec, ed;
     if (L >= 3) {
         T cp = T(0), ap = T(0), bp = T(1);
 #pragma unroll
@@ -307,8 +153,16 @@ __global__ void __launch_bounds__(TX *SEG)
         fa = a0; fb = b0; fc = c0; fd = al[0];
         ea = aL; eb = bL; ec = cL; ed = al[L - 1];
     }
+}
 
-    // ---- 2. reduced system in the segment ends
+// Reduced system of one line: the first/last rows of every segment (from segment_reduce)
+// become one tridiagonal row per segment in the segment-end unknowns E after eliminating
+// the F's; PCR across the SEG threads of the line solves it (log2 SEG rounds through
+// shared memory), then F follows from E_prev and E.  Every thread of the block calls it
+// (it synchronises the block).
+template <typename T, int TX, int SEG>
+__device__ __forceinline__ void segment_ends(T fa, T fb, T fc, T fd, T ea, T eb, T ec, T ed, int seg, int line,
+                                             T *fbuf, T *pbuf, T *ebuf, T &F, T &E) {
     const int me = seg * TX + line;
     fbuf[4 * me + 0] = fa;
     fbuf[4 * me + 1] = fb;
@@ -352,11 +206,210 @@ __global__ void __launch_bounds__(TX *SEG)
         A = -k1 * la;
         C = -k2 * uc;
     }
-    const T E = D * fast_rcp(B);
+    E = D * fast_rcp(B);
     ebuf[me] = E;
     __syncthreads();
     const T Eprev = seg > 0 ? ebuf[(seg - 1) * TX + line] : T(0);
-    const T F = (fd - fa * Eprev - fc * E) * ifb;
+    F = (fd - fa * Eprev - fc * E) * ifb;
+}
+
+template <typename T, int DIR, int TX, int SEG, int L>
+__global__ void __launch_bounds__(TX *SEG)
+    sweep_kernel(const LegDev *__restrict__ legs, int flags) {
+    static_assert(L >= 2 && L <= 30, "segment length: the row bits of a segment fit one word");
+    static_assert((SEG & (SEG - 1)) == 0, "SEG must be a power of two");
+    static_assert(32 % TX == 0, "TX divides a mask word");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+
+    const LegDev *lg = legs + blockIdx.z;
+    const int nx = lg->nx, ny = lg->ny, nz = lg->nz, pitch = lg->pitch;
+    const int wpr = mask_words_per_row(pitch);
+    const int line = threadIdx.x;
+    const int seg = threadIdx.y;
+    const int g0 = seg * L;
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    constexpr int NTHR = TX * SEG;
+    T *__restrict__ u = static_cast<T *>(lg->u);
+    const uint32_t *__restrict__ mask = lg->mask;
+    const int mid = lg->eps_mode;
+    const uint32_t *__restrict__ half = lg->half[DIR];
+    const int ndir = DIR == DIR_X ? nx : (DIR == DIR_Y ? ny : nz);
+    const T rE0 = (T)lg->rE[0], rE1 = (T)lg->rE[1], rE2 = (T)lg->rE[2];
+    const T nlq = (T)lg->nl_q, nlomq = (T)lg->nl_omq;
+    const bool nl_on = lg->nl_on != 0;
+
+    // ---- shared memory carve-up
+    T *red = reinterpret_cast<T *>(smem_raw);          // 13 * TX * SEG
+    T *fbuf = red;                                      // [SEG][TX][4]
+    T *pbuf = red + 4 * TX * SEG;                       // [2][SEG][TX][4]
+    T *ebuf = red + 12 * TX * SEG;                      // [SEG][TX]
+    T *tile = red + 13 * TX * SEG;                      // DIR_X: [TX][S]
+    const int S = sweep_tile_stride(nx, Vec16<T>::n);
+    uint32_t *smask, *shalf;
+    {
+        size_t off = (size_t)13 * TX * SEG * sizeof(T) + (DIR == DIR_X ? (size_t)TX * S * sizeof(T) : 0);
+        off = (off + 15) & ~(size_t)15;
+        smask = reinterpret_cast<uint32_t *>(smem_raw + off);
+        shalf = smask + (DIR == DIR_X ? TX * wpr : kMaxLineWords);
+    }
+
+    // ---- this thread's line
+    // element offsets within one leg fit 32 bits: at most 288^3 elements per leg
+    int lx = 0, ly = 0, lz = 0;
+    bool active;
+    int32_t base, stride;
+    if (DIR == DIR_X) {
+        ly = 1 + blockIdx.x * TX + line;
+        lz = 1 + blockIdx.y;
+        active = ly <= ny - 2;
+        base = (lz * ny + ly) * pitch;
+        stride = 1;
+    } else if (DIR == DIR_Y) {
+        lx = blockIdx.x * TX + line;
+        lz = 1 + blockIdx.y;
+        active = lx >= 1 && lx <= nx - 2;
+        base = lz * ny * pitch + lx;
+        stride = pitch;
+    } else {
+        lx = blockIdx.x * TX + line;
+        ly = 1 + blockIdx.y;
+        active = lx >= 1 && lx <= nx - 2;
+        base = ly * pitch + lx;
+        stride = ny * pitch;
+    }
+
+    // ---- stage what the block shares: X -> its TX x-rows and their mask words;
+    //      Y/Z -> the mask word column of its TX x-adjacent lines (one word per row)
+    if (DIR == DIR_X) {
+        constexpr int VEC = Vec16<T>::n;
+        using V = typename Vec16<T>::type;
+        const int nvec = (nx + VEC - 1) / VEC;
+        const int y0 = 1 + blockIdx.x * TX;
+        for (int i = tid; i < TX * nvec; i += NTHR) {
+            const int l = i / nvec, v = i - l * nvec;
+            const int y = y0 + l;
+            T vals[VEC];
+            if (y <= ny - 2) {
+                const V w = *reinterpret_cast<const V *>(u + (lz * ny + y) * pitch + v * VEC);
+                *reinterpret_cast<V *>(vals) = w;
+            } else {
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) vals[e] = T(0);
+            }
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) tile[l * S + v * VEC + e] = vals[e];
+        }
+        for (int i = tid; i < TX * wpr; i += NTHR) {
+            const int l = i / wpr, w = i - l * wpr;
+            const int y = y0 + l;
+            const int32_t row = (lz * ny + (y <= ny - 2 ? y : 0)) * wpr + w;
+            smask[i] = mask ? __ldg(mask + row) : 0xffffffffu;
+            shalf[i] = (mid && half) ? __ldg(half + row) : 0u;
+        }
+        __syncthreads();
+        if (flags & FUSE_PRE_SRC) {
+            const double src = lg->src;
+            for (int l = tid; l < TX; l += NTHR) {
+                const int y = y0 + l;
+                if (y > ny - 2) continue;
+                const int ln = lz * ny + y;
+                const int b = lg->line_begin[ln], c = lg->line_count[ln];
+                for (int e = b; e < b + c; ++e)
+                    tile[l * S + lg->ent_x[e]] += (T)(src * lg->ent_qt[e]);
+            }
+            __syncthreads();
+        }
+    } else {
+        const int wcol = (blockIdx.x * TX) >> 5;
+        for (int g = tid; g < ndir; g += NTHR) {
+            const int32_t row = DIR == DIR_Y ? (lz * ny + g) : (g * ny + ly);
+            smask[g] = mask ? __ldg(mask + row * wpr + wcol) : 0xffffffffu;
+            shalf[g] = (mid && half) ? __ldg(half + row * wpr + wcol) : 0u;
+        }
+        __syncthreads();
+    }
+
+    // ---- node bits of rows g0-1 .. g0+L (bit k+1 <-> row g0+k) and half-point bits
+    //      (bit k <-> the half point between rows g0+k-1 and g0+k)
+    uint32_t nb = 0, hb = 0;
+    if (active) {
+#pragma unroll
+        for (int k = -1; k <= L; ++k) {
+            const int g = g0 + k;
+            uint32_t bit = 1u, hbit = 0u;
+            if (g >= 0 && g < ndir) {
+                if (DIR == DIR_X) {
+                    bit = (smask[line * wpr + (g >> 5)] >> (g & 31)) & 1u;
+                    hbit = (shalf[line * wpr + (g >> 5)] >> (g & 31)) & 1u;
+                } else {
+                    bit = (smask[g] >> (lx & 31)) & 1u;
+                    hbit = (shalf[g] >> (lx & 31)) & 1u;
+                }
+            }
+            nb |= bit << (k + 1);
+            hb |= hbit << (k + 1);
+        }
+    }
+    // half point k lies between rows k-1 and k (k = 0..L): both ends inside / any end inside;
+    // in the midpoint reading the half point's own location decides
+    constexpr uint32_t kHalfMask = (L + 1 >= 32) ? 0xffffffffu : ((1u << (L + 1)) - 1u);
+    constexpr uint32_t kNodeMask = (L + 2 >= 32) ? 0xffffffffu : ((1u << (L + 2)) - 1u);
+    const uint32_t both = mid ? hb : (nb & (nb >> 1));
+    const uint32_t any = mid ? hb : (nb | (nb >> 1));
+    const bool interior_seg = g0 >= 1 && g0 + L - 1 <= ndir - 2;
+    const bool all_in = (both & kHalfMask) == kHalfMask && (nb & kNodeMask) == kNodeMask;
+    const bool all_out = (any & kHalfMask) == 0u && (nb & kNodeMask) == 0u;
+    const bool uniform = interior_seg && (all_in || all_out);
+
+    // ---- load the segment's right-hand sides
+    T al[L], be[L], ga[L];
+#pragma unroll
+    for (int k = 0; k < L; ++k) {
+        const int g = g0 + k;
+        T v = T(0);
+        if (active && g < ndir) {
+            if (DIR == DIR_X) v = tile[line * S + g];
+            else v = u[base + g * stride];
+            if ((flags & FUSE_PRE_NL) && nl_on && g >= 1 && g <= ndir - 2 && ((nb >> (k + 1)) & 1u) == 0u)
+                v = nl_flow(v, nlq, nlomq);
+        }
+        al[k] = v;
+    }
+
+    // ---- 1. local modified Thomas (constant coefficients on uniform interior segments)
+    T fa, fb, fc, fd, ea, eb, ec, ed;
+    if (uniform) {
+        const T e = all_in ? rE2 : rE0;
+        const T ca = -e, cb = T(1) + e + e;
+        auto coef = [&](int, T &a, T &b, T &c) {
+            a = ca;
+            b = cb;
+            c = ca;
+        };
+        segment_reduce<T, L>(al, be, ga, coef, fa, fb, fc, fd, ea, eb, ec, ed);
+    } else {
+        auto eh = [&](int k) -> T {
+            return ((both >> k) & 1u) ? rE2 : (((any >> k) & 1u) ? rE1 : rE0);
+        };
+        auto coef = [&](int k, T &a, T &b, T &c) {
+            const int g = g0 + k;
+            if (g < 1 || g > ndir - 2) {
+                a = T(0);
+                b = T(1);
+                c = T(0);
+                return;
+            }
+            const T em = eh(k), ep = eh(k + 1);
+            a = -em;
+            c = -ep;
+            b = T(1) + em + ep;
+        };
+        segment_reduce<T, L>(al, be, ga, coef, fa, fb, fc, fd, ea, eb, ec, ed);
+    }
+
+    // ---- 2. reduced system in the segment ends
+    T F, E;
+    segment_ends<T, TX, SEG>(fa, fb, fc, fd, ea, eb, ec, ed, seg, line, fbuf, pbuf, ebuf, F, E);
 
     // ---- 3. expand and store the interior rows
     if (DIR == DIR_X) {
@@ -372,28 +425,35 @@ __global__ void __launch_bounds__(TX *SEG)
         constexpr int VEC = Vec16<T>::n;
         using V = typename Vec16<T>::type;
         const int nvec = (nx + VEC - 1) / VEC;
-        const int tid = threadIdx.y * TX + threadIdx.x;
         const int y0 = 1 + blockIdx.x * TX;
-        for (int i = tid; i < TX * nvec; i += TX * SEG) {
+        for (int i = tid; i < TX * nvec; i += NTHR) {
             const int l = i / nvec, v = i - l * nvec;
             const int y = y0 + l;
             if (y > ny - 2) continue;
             T vals[VEC];
 #pragma unroll
             for (int e = 0; e < VEC; ++e) vals[e] = tile[l * S + v * VEC + e];
-            *reinterpret_cast<V *>(u + ((int64_t)lz * ny + y) * pitch + v * VEC) =
+            *reinterpret_cast<V *>(u + (lz * ny + y) * pitch + v * VEC) =
                 *reinterpret_cast<const V *>(vals);
         }
-    } else {
-        if (active) {
+    } else if (active) {
+        const bool post_nl = (flags & FUSE_POST_NL) && nl_on;
+        if (uniform) {
+            const bool nl_all = post_nl && all_out;
+#pragma unroll
+            for (int k = 0; k < L; ++k) {
+                T x = k == 0 ? F : (k == L - 1 ? E : al[k] + be[k] * F + ga[k] * E);
+                if (nl_all) x = nl_flow(x, nlq, nlomq);
+                u[base + (g0 + k) * stride] = x;
+            }
+        } else {
 #pragma unroll
             for (int k = 0; k < L; ++k) {
                 const int g = g0 + k;
                 if (g >= 1 && g <= ndir - 2) {
                     T x = k == 0 ? F : (k == L - 1 ? E : al[k] + be[k] * F + ga[k] * E);
-                    if ((flags & FUSE_POST_NL) && nl_on && ((nb >> (k + 1)) & 1u) == 0u)
-                        x = nl_flow(x, nlq, nlomq);
-                    u[base + (int64_t)g * stride] = x;
+                    if (post_nl && ((nb >> (k + 1)) & 1u) == 0u) x = nl_flow(x, nlq, nlomq);
+                    u[base + g * stride] = x;
                 }
             }
         }

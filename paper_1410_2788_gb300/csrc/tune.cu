@@ -29,34 +29,37 @@ extern "C" int npb_autotune(npb_grid *g, const npb_opts *o, int32_t reps, char *
     if ((rc = init_legs(g, prec, legs, 4, st))) return rc;
     const int n_dir[3] = {g->geo.nx, g->geo.ny, g->geo.nz};
     SweepShape shapes[64];
-    const int ns = sweep_shapes(prec, shapes, 64);
+    const int nc = sweep_shapes(prec, shapes, 48);
     cudaEvent_t a, b;
     CU(cudaEventCreate(&a));
     CU(cudaEventCreate(&b));
     std::string rep = "[";
     for (int d = 0; d < 3; ++d) {
-        SweepShape best{0, 0, 0};
+        int ns = nc;
+        if (prec == NPB_FP32_SWEEP && g->tma_ok[d]) ns += tma_shapes(d, shapes + nc, 64 - nc);
+        SweepShape best{0, 0, 0, 0};
         float best_ms = 1e30f;
         for (int i = 0; i < ns; ++i) {
             const SweepShape s = shapes[i];
             if (s.seg * s.len < n_dir[d]) continue;
             if (s.seg * s.len > 2 * n_dir[d] + 32) continue;  // mostly padding: never faster
-            cudaError_t e = launch_sweep(prec, d, g->d_legs[prec], 4, g->geo.nx, g->geo.ny, g->geo.nz, 0, s, st);
+            cudaError_t e = launch_dir(g, prec, d, s, 0, 4, 0, st);
             if (e != cudaSuccess) {
                 cudaGetLastError();
                 continue;
             }
             CU(cudaEventRecord(a, st));
             for (int r = 0; r < reps; ++r)
-                CU(launch_sweep(prec, d, g->d_legs[prec], 4, g->geo.nx, g->geo.ny, g->geo.nz, 0, s, st));
+                CU(launch_dir(g, prec, d, s, 0, 4, 0, st));
             CU(cudaEventRecord(b, st));
             CU(cudaEventSynchronize(b));
             float ms = 0.f;
             CU(cudaEventElapsedTime(&ms, a, b));
             ms /= reps;
             char buf[160];
-            snprintf(buf, sizeof buf, "%s{\"dir\":%d,\"n\":%d,\"tx\":%d,\"seg\":%d,\"len\":%d,\"ms\":%.5f}",
-                     rep.size() > 1 ? "," : "", d, n_dir[d], s.tx, s.seg, s.len, ms);
+            snprintf(buf, sizeof buf,
+                     "%s{\"dir\":%d,\"n\":%d,\"tx\":%d,\"seg\":%d,\"len\":%d,\"kind\":%d,\"ms\":%.5f}",
+                     rep.size() > 1 ? "," : "", d, n_dir[d], s.tx, s.seg, s.len, s.kind, ms);
             rep += buf;
             if (ms < best_ms) {
                 best_ms = ms;
@@ -83,8 +86,14 @@ extern "C" int npb_autotune(npb_grid *g, const npb_opts *o, int32_t reps, char *
 extern "C" int npb_tune_set(npb_ctx *ctx, int32_t precision, int32_t dir, int32_t n, int32_t tx, int32_t seg,
                             int32_t len) {
     if (!ctx || dir < 0 || dir > 2) return fail(NPB_EINVAL, "bad argument");
-    SweepShape s{tx, seg, len};
-    if (!sweep_shape_available(precision, s)) return fail(NPB_EINVAL, "shape %d/%d/%d not instantiated", tx, seg, len);
+    SweepShape s{tx, seg, len, 0};
+    if (!sweep_shape_available(precision, s)) {
+        SweepShape t[16];
+        const int k = precision == NPB_FP32_SWEEP ? tma_shapes(dir, t, 16) : 0;
+        for (int i = 0; i < k; ++i)
+            if (t[i].tx == tx && t[i].seg == seg && t[i].len == len) s = t[i];
+        if (s.kind == 0) return fail(NPB_EINVAL, "shape %d/%d/%d not instantiated", tx, seg, len);
+    }
     if (seg * len < n) return fail(NPB_EINVAL, "shape covers %d rows < n = %d", seg * len, n);
     std::lock_guard<std::mutex> lk(ctx->tune_mu);
     ctx->tuned[tune_key(precision, dir, n)] = s;

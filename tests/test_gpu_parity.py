@@ -186,6 +186,8 @@ def _energy_case(npb, ctx, O, p, dt, alpha, n, richardson=True, eps_mode=0, sche
                         solvent_far = far & (st.in_mol == 0)
                         entry["abs_solvent_far"] = float(diff[solvent_far].max()) if solvent_far.any() else 0.0
                         entry["max_u_solvent_far"] = float(np.abs(ref[solvent_far]).max()) if solvent_far.any() else 0.0
+                        # kT/e: absolute where |u| <= 1 there, relative to the region's largest |u| above
+                        assert entry["abs_solvent_far"] <= 1e-4 * max(1.0, entry["max_u_solvent_far"]), (leg, entry)
                     report[prec][f"leg{leg}"] = entry
                     assert far_abs <= 1e-4 * max(1.0, float(np.abs(ref[far]).max())), (leg, far_abs)
     finally:
