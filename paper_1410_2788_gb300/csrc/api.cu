@@ -345,6 +345,8 @@ int npb::grid_build(npb_ctx *ctx, const npb_problem *p, cudaStream_t st, npb_gri
     if ((rc = galloc(g, &g->d_q, std::max(1, na)))) return guard(rc);
     if ((rc = galloc(g, &g->d_rad, std::max(1, na)))) return guard(rc);
     if ((rc = galloc(g, &g->d_mask, words))) return guard(rc);
+    if ((rc = galloc(g, &g->d_mask_y, (size_t)g->geo.nz * g->geo.nx * line_words(g->geo.ny)))) return guard(rc);
+    if ((rc = galloc(g, &g->d_mask_z, (size_t)g->geo.ny * g->geo.nx * line_words(g->geo.nz)))) return guard(rc);
     if ((rc = galloc(g, &g->d_line_begin, n_lines))) return guard(rc);
     if ((rc = galloc(g, &g->d_line_count, n_lines))) return guard(rc);
     const int n_raw = std::max(1, 8 * na);
@@ -396,10 +398,13 @@ int npb::grid_setup(npb_grid *g, cudaStream_t st) {
     int rc;
     cudaEvent_t ev{};
     CU(cudaMemsetAsync(g->d_mask, 0, words * 4, st));
+    CU(cudaMemsetAsync(g->d_mask_y, 0, sizeof(uint32_t) * g->geo.nz * g->geo.nx * line_words(g->geo.ny), st));
+    CU(cudaMemsetAsync(g->d_mask_z, 0, sizeof(uint32_t) * g->geo.ny * g->geo.nx * line_words(g->geo.nz), st));
     for (int d = 0; d < 3; ++d)
         if (g->d_half[d]) CU(cudaMemsetAsync(g->d_half[d], 0, words * 4, st));
     if ((rc = pr.begin(st, &ev))) return rc;
-    CU(setup_mask(g->geo, g->d_xyz, g->d_rad, na, g->d_mask, g->d_half[0], g->d_half[1], g->d_half[2], st));
+    CU(setup_mask(g->geo, g->d_xyz, g->d_rad, na, g->d_mask, g->d_half[0], g->d_half[1], g->d_half[2], g->d_mask_y,
+                  g->d_mask_z, st));
     if ((rc = pr.end(st, ev, K_SETUP_MASK))) return rc;
     if ((rc = pr.begin(st, &ev))) return rc;
     CU(setup_charges(g->geo, g->d_xyz, g->d_q, na, g->sc, g->d_line_begin, g->d_line_count, g->d_ent_x,
@@ -457,7 +462,7 @@ int npb::grid_half_masks(npb_grid *g, cudaStream_t st) {
     }
     // the node mask is rebuilt alongside (atomicOr keeps it identical)
     CU(setup_mask(g->geo, g->d_xyz, g->d_rad, g->n_atoms, g->d_mask, g->d_half[0], g->d_half[1], g->d_half[2],
-                  st));
+                  nullptr, nullptr, st));
     return 0;
 }
 
@@ -581,9 +586,13 @@ int npb::grid_tma(npb_grid *g) {
     for (int d = 0; d < 3; ++d) {
         g->tma_g[d] = tma_geometry(d, nx, ny, nz, pitch);
         bool ok = g->tma_g[d].ok && g->d_u[NPB_FP32_SWEEP][0] != nullptr;
-        for (int s = 0; s < 4 && ok; ++s)
-            ok = tma_encode_state(&g->tma_u[d][s], g->d_u[NPB_FP32_SWEEP][s], d, g->tma_g[d], nx, ny, nz, pitch);
-        if (ok) ok = tma_encode_mask(&g->tma_m[d], g->d_mask, d, g->tma_g[d], ny, nz);
+        const uint32_t *lm = d == 0 ? g->d_mask : (d == 1 ? g->d_mask_y : g->d_mask_z);
+        for (int v = 0; v < 2 && ok; ++v) {  // x: 8 lines per tile; y/z: 32 or 16
+            for (int s = 0; s < 4 && ok; ++s)
+                ok = tma_encode_state(&g->tma_u[d][v][s], g->d_u[NPB_FP32_SWEEP][s], d, g->tma_g[d], nx, ny, nz,
+                                      pitch, tma_variant_tx(d, v));
+            if (ok) ok = tma_encode_mask(&g->tma_m[d][v], lm, d, g->tma_g[d], nx, ny, nz, tma_variant_tx(d, v));
+        }
         g->tma_ok[d] = ok;
     }
     return 0;
@@ -600,9 +609,11 @@ cudaError_t npb::launch_dir(npb_grid *g, int prec, int d, SweepShape shape, int 
         g->h_legs[prec][slot0].eps_mode == 0) {
         TmaLaunch P;
         memset(&P, 0, sizeof P);
+        const int v = tma_variant(d, shape.tx);
+        if (v < 0) return cudaErrorInvalidValue;
         for (int i = 0; i < n_legs; ++i) {
-            P.umap[i] = g->tma_u[d][slot0 + i];
-            P.mmap[i] = g->tma_m[d];
+            P.umap[i] = g->tma_u[d][v][slot0 + i];
+            P.mmap[i] = g->tma_m[d][v];
             P.legs[i] = g->h_legs[prec][slot0 + i];
         }
         P.n_legs = n_legs;

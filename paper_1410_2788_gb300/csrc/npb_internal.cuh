@@ -29,6 +29,11 @@ enum Dir { DIR_X = 0, DIR_Y = 1, DIR_Z = 2 };
 // uint32 words per x-row of a bit array: pitch/32 rounded up to a multiple of 4.
 __host__ __device__ __forceinline__ int mask_words_per_row(int pitch) { return ((pitch >> 5) + 3) & ~3; }
 
+// uint32 words per line of a line-major bit array along a line of n nodes: ceil(n/32)
+// rounded up to a multiple of 4 (16-byte lines).  The y-major mask is [nz][nx][words(ny)]
+// (bit y of line (x, z)), the z-major mask [ny][nx][words(nz)] (bit z of line (x, y)).
+__host__ __device__ __forceinline__ int line_words(int n) { return (((n + 31) >> 5) + 3) & ~3; }
+
 // Everything a sweep / stage kernel needs for one leg.  Lives in device memory as an
 // array indexed by blockIdx.z, so one launch can advance several legs of equal size.
 struct LegDev {

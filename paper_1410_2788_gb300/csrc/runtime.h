@@ -91,6 +91,8 @@ struct npb_grid {
     int n_atoms = 0;
     double *d_xyz = nullptr, *d_q = nullptr, *d_rad = nullptr;
     uint32_t *d_mask = nullptr;
+    uint32_t *d_mask_y = nullptr;  // line-major copies of the node mask for the y and z sweeps
+    uint32_t *d_mask_z = nullptr;
     uint32_t *d_half[3] = {nullptr, nullptr, nullptr};
     int32_t *d_line_begin = nullptr, *d_line_count = nullptr, *d_ent_x = nullptr;
     double *d_ent_qt = nullptr;
@@ -106,8 +108,8 @@ struct npb_grid {
     double *d_result = nullptr;
     double *h_result = nullptr;  // pinned
     int32_t *d_err = nullptr;    // set by a device wait that expired
-    CUtensorMap tma_u[3][4];     // FP32 leg states by [direction][slot]
-    CUtensorMap tma_m[3];        // node mask by direction
+    CUtensorMap tma_u[3][2][4];  // FP32 leg states by [direction][lines-per-tile variant][slot]
+    CUtensorMap tma_m[3][2];     // line-major mask by [direction][variant]
     npb::TmaGeom tma_g[3] = {};
     bool tma_ok[3] = {false, false, false};
     bool tma_built = false;

@@ -30,7 +30,8 @@ __device__ __forceinline__ double dist2(double dx, double dy, double dz) {
 __global__ void k_mask_atoms(GridGeom g, const double *__restrict__ xyz,
                              const double *__restrict__ radius, int n_atoms,
                              uint32_t *__restrict__ mask, uint32_t *__restrict__ hx,
-                             uint32_t *__restrict__ hy, uint32_t *__restrict__ hz) {
+                             uint32_t *__restrict__ hy, uint32_t *__restrict__ hz,
+                             uint32_t *__restrict__ my, uint32_t *__restrict__ mz) {
     const int a = blockIdx.x;
     if (a >= n_atoms) return;
     const double c[3] = {xyz[3 * a], xyz[3 * a + 1], xyz[3 * a + 2]};
@@ -49,6 +50,7 @@ __global__ void k_mask_atoms(GridGeom g, const double *__restrict__ xyz,
     if (ex <= 0 || ey <= 0 || ez <= 0) return;
     const int total = ex * ey * ez;
     const int wpr = mask_words_per_row(g.pitch);
+    const int wy = line_words(g.ny), wz = line_words(g.nz);
     const double hh = __dmul_rn(0.5, g.h);
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
         const int i = lo[0] + t % ex;
@@ -58,8 +60,11 @@ __global__ void k_mask_atoms(GridGeom g, const double *__restrict__ xyz,
                      pz = node_coord(o[2], k, g.h);
         const int64_t w = ((int64_t)k * g.ny + j) * wpr + (i >> 5);
         const uint32_t bit = 1u << (i & 31);
-        if (dist2(__dsub_rn(px, c[0]), __dsub_rn(py, c[1]), __dsub_rn(pz, c[2])) <= r2)
+        if (dist2(__dsub_rn(px, c[0]), __dsub_rn(py, c[1]), __dsub_rn(pz, c[2])) <= r2) {
             atomicOr(mask + w, bit);
+            if (my) atomicOr(my + ((int64_t)k * g.nx + i) * wy + (j >> 5), 1u << (j & 31));
+            if (mz) atomicOr(mz + ((int64_t)j * g.nx + i) * wz + (k >> 5), 1u << (k & 31));
+        }
         if (hx) {
             if (dist2(__dsub_rn(__dadd_rn(px, hh), c[0]), __dsub_rn(py, c[1]), __dsub_rn(pz, c[2])) <= r2)
                 atomicOr(hx + w, bit);
@@ -357,8 +362,9 @@ __global__ void k_qt_dense(GridGeom g, const int32_t *__restrict__ line_begin,
 static inline int blocks_for(int64_t n, int t) { return (int)std::min<int64_t>((n + t - 1) / t, 1 << 20); }
 
 cudaError_t setup_mask(const GridGeom &g, const double *xyz, const double *radius, int n_atoms,
-                       uint32_t *mask, uint32_t *hx, uint32_t *hy, uint32_t *hz, cudaStream_t st) {
-    if (n_atoms > 0) k_mask_atoms<<<n_atoms, 256, 0, st>>>(g, xyz, radius, n_atoms, mask, hx, hy, hz);
+                       uint32_t *mask, uint32_t *hx, uint32_t *hy, uint32_t *hz, uint32_t *my, uint32_t *mz,
+                       cudaStream_t st) {
+    if (n_atoms > 0) k_mask_atoms<<<n_atoms, 256, 0, st>>>(g, xyz, radius, n_atoms, mask, hx, hy, hz, my, mz);
     return cudaGetLastError();
 }
 

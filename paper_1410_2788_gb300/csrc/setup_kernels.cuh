@@ -28,7 +28,8 @@ struct ChargeScratch {  // device scratch used while building the charge list
 __host__ __device__ int64_t face_count(int nx, int ny, int nz);
 
 cudaError_t setup_mask(const GridGeom &g, const double *xyz, const double *radius, int n_atoms,
-                       uint32_t *mask, uint32_t *hx, uint32_t *hy, uint32_t *hz, cudaStream_t st);
+                       uint32_t *mask, uint32_t *hx, uint32_t *hy, uint32_t *hz, uint32_t *my, uint32_t *mz,
+                       cudaStream_t st);
 cudaError_t setup_charges(const GridGeom &g, const double *xyz, const double *q, int n_atoms,
                           ChargeScratch &s, int32_t *line_begin, int32_t *line_count, int32_t *ent_x,
                           double *ent_qt, int64_t *ent_off, cudaStream_t st);

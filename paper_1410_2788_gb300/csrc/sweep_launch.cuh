@@ -40,6 +40,16 @@ template <typename T, int TX, int SEG, int L>
 static cudaError_t prepare_shape() {
     cudaError_t e = cudaSuccess;
     const int big = 200 * 1024;
+    const int carve = cudaSharedmemCarveoutMaxShared;
+    e = cudaFuncSetAttribute(sweep_kernel<T, DIR_X, TX, SEG, L>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             carve);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sweep_kernel<T, DIR_Y, TX, SEG, L>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 carve);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sweep_kernel<T, DIR_Z, TX, SEG, L>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 carve);
+    if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(sweep_kernel<T, DIR_X, TX, SEG, L>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     if (e == cudaSuccess)

@@ -119,16 +119,30 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 
 __host__ __device__ __forceinline__ size_t tma_align(size_t b) { return (b + 127) & ~(size_t)127; }
 
-// Every bulk tensor copy into shared memory starts on a 128-byte boundary: stage buffers are
-// 128-aligned, the y/z state boxes are 128*rows bytes apart (32 floats per row), and the
-// y/z mask boxes sit tma_align(16*rows) bytes apart.
-__host__ __device__ __forceinline__ size_t tma_mask_box_bytes(int rows) { return tma_align((size_t)rows * 16); }
+// Every bulk tensor copy into shared memory starts on a 128-byte boundary: the stage buffers
+// are 128-aligned, and the y/z state boxes of a tile follow each other contiguously, each
+// rows*tx*4 bytes long -- a multiple of 128 (tx = 32, or tx = 16 with an even row count), so
+// row g of the tile is element g*tx + line whichever box holds it.
+__host__ __device__ __forceinline__ size_t tma_data_box_bytes(int rows, int tx) { return (size_t)rows * tx * 4; }
 
 template <int DIR, int TX, int SEG>
 __host__ __device__ __forceinline__ size_t tma_smem_bytes(int rows, int nload, int sx, int mwpr) {
-    const size_t data = DIR == DIR_X ? (size_t)TX * sx * 4 : (size_t)nload * rows * TX * 4;
-    const size_t mask = DIR == DIR_X ? (size_t)TX * mwpr * 4 : (size_t)nload * tma_mask_box_bytes(rows);
+    const size_t data = DIR == DIR_X ? (size_t)TX * sx * 4 : (size_t)nload * tma_data_box_bytes(rows, TX);
+    const size_t mask = (size_t)TX * mwpr * 4;
     return 128 + 2 * (tma_align(data) + tma_align(mask)) + tma_align((size_t)13 * TX * SEG * 4) + 64;
+}
+
+// Bits of rows g0-1 .. g0+L of one line (bit k+1 <-> row g0+k) from its line-major words.
+// Row -1 does not exist; its bit never matters because row 0 is a face row.
+__device__ __forceinline__ uint32_t segment_bits(const uint32_t *W, int nwords, int g0) {
+    const int s = g0 - 1;
+    const int s0 = s < 0 ? 0 : s;
+    const int w = s0 >> 5;
+    const uint32_t lo = w < nwords ? W[w] : 0u;
+    const uint32_t hi = w + 1 < nwords ? W[w + 1] : 0u;
+    const uint64_t v = ((uint64_t)hi << 32) | lo;
+    if (s < 0) return ((uint32_t)v << 1) | 1u;
+    return (uint32_t)(v >> (s & 31));
 }
 
 template <int DIR, int TX, int SEG, int L>
@@ -140,9 +154,9 @@ __global__ void __launch_bounds__(TX *SEG) sweep_tma_kernel(const __grid_constan
 
     const int tid = threadIdx.y * TX + threadIdx.x;
     const int line = threadIdx.x, seg = threadIdx.y, g0 = seg * L;
-    const size_t data_b = DIR == DIR_X ? (size_t)TX * P.sx * 4 : (size_t)P.nload * P.rows * TX * 4;
-    const size_t mbox = tma_mask_box_bytes(P.rows);  // y/z: bytes between the mask boxes
-    const size_t mask_b = DIR == DIR_X ? (size_t)TX * P.mwpr * 4 : (size_t)P.nload * mbox;
+    const size_t dbox = DIR == DIR_X ? 0 : tma_data_box_bytes(P.rows, TX);  // bytes between state boxes
+    const size_t data_b = DIR == DIR_X ? (size_t)TX * P.sx * 4 : (size_t)P.nload * dbox;
+    const size_t mask_b = (size_t)TX * P.mwpr * 4;
     T *data[2];
     uint32_t *msk[2];
     // round the dynamic shared base up to 128 bytes (128 spare bytes are requested for this)
@@ -157,6 +171,9 @@ __global__ void __launch_bounds__(TX *SEG) sweep_tma_kernel(const __grid_constan
     off += tma_align((size_t)13 * TX * SEG * 4);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + off);
     T *fbuf = red, *pbuf = red + 4 * TX * SEG, *ebuf = red + 12 * TX * SEG;
+    const int dboxf = (int)(dbox / 4);
+    // shared-memory element of row g of this thread's line
+    auto at = [&](int g) -> int { return DIR == DIR_X ? line * P.sx + g : g * TX + line; };
 
     if (tid == 0) {
         mbar_init(&bar[0], 1);
@@ -177,17 +194,14 @@ __global__ void __launch_bounds__(TX *SEG) sweep_tma_kernel(const __grid_constan
             tma_load_4d(data[s], &P.umap[leg], &bar[s], 0, 0, y0, z);
             if (has_mask) tma_load_3d(msk[s], &P.mmap[leg], &bar[s], 0, y0, z);
         } else {
-            const int x0 = a * TX, w4 = (x0 >> 5) & ~3, c = 1 + b;
+            const int x0 = a * TX, c = 1 + b;
             for (int q = 0; q < P.nload; ++q) {
                 const int r0 = q * P.rows;
-                if (DIR == DIR_Y) {
-                    tma_load_3d(data[s] + (size_t)r0 * TX, &P.umap[leg], &bar[s], x0, r0, c);
-                    if (has_mask) tma_load_3d(msk[s] + q * (mbox / 4), &P.mmap[leg], &bar[s], w4, r0, c);
-                } else {
-                    tma_load_3d(data[s] + (size_t)r0 * TX, &P.umap[leg], &bar[s], x0, c, r0);
-                    if (has_mask) tma_load_3d(msk[s] + q * (mbox / 4), &P.mmap[leg], &bar[s], w4, c, r0);
-                }
+                T *dst = data[s] + (size_t)q * dboxf;
+                if (DIR == DIR_Y) tma_load_3d(dst, &P.umap[leg], &bar[s], x0, r0, c);
+                else tma_load_3d(dst, &P.umap[leg], &bar[s], x0, c, r0);
             }
+            if (has_mask) tma_load_3d(msk[s], &P.mmap[leg], &bar[s], 0, x0, c);
         }
     };
 
@@ -220,56 +234,30 @@ __global__ void __launch_bounds__(TX *SEG) sweep_tma_kernel(const __grid_constan
         const bool nl_on = lg.nl_on != 0;
         const bool has_mask = lg.mask != nullptr;
         T *D = data[s];
-        const uint32_t *M = msk[s];
-        int lx = 0;
-        bool active;
-        if (DIR == DIR_X) {
-            active = 1 + a * TX + line <= ny - 2;
-        } else {
-            lx = a * TX + line;
-            active = lx >= 1 && lx <= nx - 2;
-        }
-        const int wsel = DIR == DIR_X ? 0 : (((a * TX) >> 5) & 3);
+        const bool active = DIR == DIR_X ? (1 + a * TX + line <= ny - 2)
+                                         : (a * TX + line >= 1 && a * TX + line <= nx - 2);
 
-        uint32_t nb = 0;
-        if (active) {
-#pragma unroll
-            for (int k = -1; k <= L; ++k) {
-                const int g = g0 + k;
-                uint32_t bit = 1u;
-                if (has_mask && g >= 0 && g < ndir) {
-                    if (DIR == DIR_X) bit = (M[line * P.mwpr + (g >> 5)] >> (g & 31)) & 1u;
-                    else {
-                        const int q = g >= P.rows ? 1 : 0;  // which mask box holds row g
-                        bit = (M[q * (mbox / 4) + (g - q * P.rows) * 4 + wsel] >> (lx & 31)) & 1u;
-                    }
-                }
-                nb |= bit << (k + 1);
-            }
-        }
+        const uint32_t nb = !active ? 0u : (has_mask ? segment_bits(msk[s] + line * P.mwpr, P.mwpr, g0) : 0xffffffffu);
         constexpr uint32_t kHalfMask = (1u << (L + 1)) - 1u;
         constexpr uint32_t kNodeMask = (1u << (L + 2)) - 1u;
         const uint32_t both = nb & (nb >> 1), any = nb | (nb >> 1);
         const bool interior_seg = g0 >= 1 && g0 + L - 1 <= ndir - 2;
         const bool all_in = (both & kHalfMask) == kHalfMask && (nb & kNodeMask) == kNodeMask;
         const bool all_out = (any & kHalfMask) == 0u && (nb & kNodeMask) == 0u;
-        const bool uniform = interior_seg && (all_in || all_out);
+        const bool uniform = active && interior_seg && (all_in || all_out);
+        const bool pre_nl = (flags & FUSE_PRE_NL) && nl_on;
+        const bool post_nl = (flags & FUSE_POST_NL) && nl_on;
 
         T al[L], be[L], ga[L];
-#pragma unroll
-        for (int k = 0; k < L; ++k) {
-            const int g = g0 + k;
-            T v = T(0);
-            if (active && g < ndir) {
-                v = DIR == DIR_X ? D[line * P.sx + g] : D[g * TX + line];
-                if ((flags & FUSE_PRE_NL) && nl_on && g >= 1 && g <= ndir - 2 && ((nb >> (k + 1)) & 1u) == 0u)
-                    v = nl_flow(v, nlq, nlomq);
-            }
-            al[k] = v;
-        }
-
         T fa, fb, fc, fd, ea, eb, ec, ed;
         if (uniform) {
+            // every row is an interior row with the same coefficients
+            const bool nl_rows = pre_nl && all_out;
+#pragma unroll
+            for (int k = 0; k < L; ++k) {
+                const T v = D[at(g0 + k)];
+                al[k] = nl_rows ? nl_flow(v, nlq, nlomq) : v;
+            }
             const T e = all_in ? rE2 : rE0;
             const T ca = -e, cb = T(1) + e + e;
             auto coef = [&](int, T &ca_, T &cb_, T &cc_) {
@@ -279,6 +267,16 @@ __global__ void __launch_bounds__(TX *SEG) sweep_tma_kernel(const __grid_constan
             };
             segment_reduce<T, L>(al, be, ga, coef, fa, fb, fc, fd, ea, eb, ec, ed);
         } else {
+#pragma unroll
+            for (int k = 0; k < L; ++k) {
+                const int g = g0 + k;
+                T v = T(0);
+                if (active && g < ndir) {
+                    v = D[at(g)];
+                    if (pre_nl && g >= 1 && g <= ndir - 2 && ((nb >> (k + 1)) & 1u) == 0u) v = nl_flow(v, nlq, nlomq);
+                }
+                al[k] = v;
+            }
             auto eh = [&](int k) -> T {
                 return ((both >> k) & 1u) ? rE2 : (((any >> k) & 1u) ? rE1 : rE0);
             };
@@ -300,16 +298,22 @@ __global__ void __launch_bounds__(TX *SEG) sweep_tma_kernel(const __grid_constan
         T F, E;
         segment_ends<T, TX, SEG>(fa, fb, fc, fd, ea, eb, ec, ed, seg, line, fbuf, pbuf, ebuf, F, E);
 
-        if (active) {
-            const bool post_nl = (flags & FUSE_POST_NL) && nl_on;
+        if (uniform) {
+            const bool nl_rows = post_nl && all_out;
+#pragma unroll
+            for (int k = 0; k < L; ++k) {
+                T x = k == 0 ? F : (k == L - 1 ? E : al[k] + be[k] * F + ga[k] * E);
+                if (nl_rows) x = nl_flow(x, nlq, nlomq);
+                D[at(g0 + k)] = x;
+            }
+        } else if (active) {
 #pragma unroll
             for (int k = 0; k < L; ++k) {
                 const int g = g0 + k;
                 if (g >= 1 && g <= ndir - 2) {
                     T x = k == 0 ? F : (k == L - 1 ? E : al[k] + be[k] * F + ga[k] * E);
                     if (post_nl && ((nb >> (k + 1)) & 1u) == 0u) x = nl_flow(x, nlq, nlomq);
-                    if (DIR == DIR_X) D[line * P.sx + g] = x;
-                    else D[g * TX + line] = x;
+                    D[at(g)] = x;
                 }
             }
         }
@@ -322,8 +326,9 @@ __global__ void __launch_bounds__(TX *SEG) sweep_tma_kernel(const __grid_constan
                 const int x0 = a * TX, c = 1 + bb;
                 for (int q = 0; q < P.nload; ++q) {
                     const int r0 = q * P.rows;
-                    if (DIR == DIR_Y) tma_store_3d(&P.umap[leg], D + (size_t)r0 * TX, x0, r0, c);
-                    else tma_store_3d(&P.umap[leg], D + (size_t)r0 * TX, x0, c, r0);
+                    const T *src = D + (size_t)q * dboxf;
+                    if (DIR == DIR_Y) tma_store_3d(&P.umap[leg], src, x0, r0, c);
+                    else tma_store_3d(&P.umap[leg], src, x0, c, r0);
                 }
             }
             bulk_commit();

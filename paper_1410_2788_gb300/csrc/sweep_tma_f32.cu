@@ -12,12 +12,15 @@ namespace npb {
 
 // Instantiated TMA shapes: x sweeps use 8 lines per tile, y/z sweeps 32.
 #define NPB_TMA_X_SHAPES(X) X(8, 2, 17) X(8, 4, 9) X(8, 4, 17) X(8, 8, 13) X(8, 8, 17) X(8, 16, 11) X(8, 16, 17) X(8, 32, 9)
-#define NPB_TMA_YZ_SHAPES(X) X(32, 2, 17) X(32, 4, 9) X(32, 4, 17) X(32, 8, 13) X(32, 8, 17) X(32, 16, 11) X(32, 16, 17)
+#define NPB_TMA_YZ_SHAPES(X) X(32, 2, 17) X(32, 4, 9) X(32, 4, 17) X(32, 8, 13) X(32, 8, 17) X(32, 16, 11) X(32, 16, 17) \
+    X(16, 4, 17) X(16, 8, 13) X(16, 8, 17) X(16, 16, 11) X(16, 16, 17) X(16, 32, 9)
 
 static const SweepShape kTmaX[] = {{8, 2, 17, 1}, {8, 4, 9, 1}, {8, 4, 17, 1}, {8, 8, 13, 1},
                                    {8, 8, 17, 1}, {8, 16, 11, 1}, {8, 16, 17, 1}, {8, 32, 9, 1}};
-static const SweepShape kTmaYZ[] = {{32, 2, 17, 1}, {32, 4, 9, 1}, {32, 4, 17, 1}, {32, 8, 13, 1},
-                                    {32, 8, 17, 1}, {32, 16, 11, 1}, {32, 16, 17, 1}};
+static const SweepShape kTmaYZ[] = {{32, 2, 17, 1}, {32, 4, 9, 1},  {32, 4, 17, 1},  {32, 8, 13, 1},
+                                    {32, 8, 17, 1}, {32, 16, 11, 1}, {32, 16, 17, 1}, {16, 4, 17, 1},
+                                    {16, 8, 13, 1}, {16, 8, 17, 1},  {16, 16, 11, 1}, {16, 16, 17, 1},
+                                    {16, 32, 9, 1}};
 
 int tma_shapes(int dir, SweepShape *out, int max) {
     int n = 0;
@@ -49,7 +52,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 encoder() {
 // xc a multiple of 4 and at most 256 (a TMA box dimension).  y/z: rows per box <= 256.
 TmaGeom tma_geometry(int dir, int nx, int ny, int nz, int pitch) {
     TmaGeom g{};
-    g.mwpr = mask_words_per_row(pitch);
+    g.mwpr = dir == DIR_X ? mask_words_per_row(pitch) : line_words(dir == DIR_Y ? ny : nz);
     if (dir == DIR_X) {
         for (int sx = (nx + 3) / 4 * 4; sx <= pitch && !g.ok; sx += 4) {
             if (sx % 8 != 4) continue;
@@ -67,12 +70,14 @@ TmaGeom tma_geometry(int dir, int nx, int ny, int nz, int pitch) {
         const int n = dir == DIR_Y ? ny : nz;
         g.nload = (n + 255) / 256;
         g.rows = (n + g.nload - 1) / g.nload;
-        g.ok = g.nload <= 2;
+        if (g.nload > 1) g.rows = (g.rows + 1) & ~1;  // even: boxes of 16 lines stay 128-byte multiples
+        g.ok = g.nload <= 2 && g.rows <= 256;
     }
     return g;
 }
 
-bool tma_encode_state(CUtensorMap *m, void *u, int dir, const TmaGeom &g, int nx, int ny, int nz, int pitch) {
+bool tma_encode_state(CUtensorMap *m, void *u, int dir, const TmaGeom &g, int nx, int ny, int nz, int pitch,
+                      int tx) {
     auto enc = encoder();
     if (!enc || !g.ok) return false;
     (void)nx;
@@ -81,35 +86,32 @@ bool tma_encode_state(CUtensorMap *m, void *u, int dir, const TmaGeom &g, int nx
     if (dir == DIR_X) {
         const cuuint64_t dims[4] = {(cuuint64_t)g.xc, (cuuint64_t)g.nchunk, (cuuint64_t)ny, (cuuint64_t)nz};
         const cuuint64_t strides[3] = {(cuuint64_t)g.xc * 4, (cuuint64_t)pitch * 4, (cuuint64_t)ny * pitch * 4};
-        const cuuint32_t box[4] = {(cuuint32_t)g.xc, (cuuint32_t)g.nchunk, 8, 1};
+        const cuuint32_t box[4] = {(cuuint32_t)g.xc, (cuuint32_t)g.nchunk, (cuuint32_t)tx, 1};
         r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, u, dims, strides, box, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
                 CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     } else {
         const cuuint64_t dims[3] = {(cuuint64_t)pitch, (cuuint64_t)ny, (cuuint64_t)nz};
         const cuuint64_t strides[2] = {(cuuint64_t)pitch * 4, (cuuint64_t)ny * pitch * 4};
-        const cuuint32_t box[3] = {32, dir == DIR_Y ? (cuuint32_t)g.rows : 1u, dir == DIR_Z ? (cuuint32_t)g.rows : 1u};
+        const cuuint32_t box[3] = {(cuuint32_t)tx, dir == DIR_Y ? (cuuint32_t)g.rows : 1u,
+                                   dir == DIR_Z ? (cuuint32_t)g.rows : 1u};
         r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, u, dims, strides, box, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
                 CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     }
     return r == CUDA_SUCCESS;
 }
 
-bool tma_encode_mask(CUtensorMap *m, const uint32_t *mask, int dir, const TmaGeom &g, int ny, int nz) {
+// The mask of direction d as a line-major bit array: x -> the node mask [nz][ny][words(pitch)],
+// y -> [nz][nx][words(ny)], z -> [ny][nx][words(nz)].  One box holds all the bits of the tile's
+// lines: {words, tx lines, 1}.
+bool tma_encode_mask(CUtensorMap *m, const uint32_t *mask, int dir, const TmaGeom &g, int nx, int ny, int nz, int tx) {
     auto enc = encoder();
     if (!enc || !g.ok) return false;
     const cuuint32_t one[3] = {1, 1, 1};
-    const cuuint64_t dims[3] = {(cuuint64_t)g.mwpr, (cuuint64_t)ny, (cuuint64_t)nz};
-    const cuuint64_t strides[2] = {(cuuint64_t)g.mwpr * 4, (cuuint64_t)ny * g.mwpr * 4};
-    cuuint32_t box[3];
-    if (dir == DIR_X) {
-        box[0] = (cuuint32_t)g.mwpr;
-        box[1] = 8;
-        box[2] = 1;
-    } else {
-        box[0] = 4;
-        box[1] = dir == DIR_Y ? (cuuint32_t)g.rows : 1u;
-        box[2] = dir == DIR_Z ? (cuuint32_t)g.rows : 1u;
-    }
+    const cuuint64_t lines = dir == DIR_X ? (cuuint64_t)ny : (cuuint64_t)nx;
+    const cuuint64_t planes = dir == DIR_Z ? (cuuint64_t)ny : (cuuint64_t)nz;
+    const cuuint64_t dims[3] = {(cuuint64_t)g.mwpr, lines, planes};
+    const cuuint64_t strides[2] = {(cuuint64_t)g.mwpr * 4, lines * g.mwpr * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)g.mwpr, (cuuint32_t)tx, 1};
     CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, const_cast<uint32_t *>(mask), dims, strides, box, one,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -121,8 +123,7 @@ static cudaError_t launch_tma_shape(const TmaLaunch &P, const TmaGeom &g, int fl
     const size_t smem = tma_smem_bytes<DIR, TX, SEG>(g.rows, g.nload, g.sx, g.mwpr);
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
     // every shared-memory destination of a bulk tensor copy must sit on a 128-byte boundary
-    if (DIR != DIR_X && (((size_t)g.rows * TX * 4) % 128 || tma_mask_box_bytes(g.rows) % 128))
-        return cudaErrorInvalidValue;
+    if (DIR != DIR_X && g.nload > 1 && tma_data_box_bytes(g.rows, TX) % 128) return cudaErrorInvalidValue;
     auto kern = sweep_tma_kernel<DIR, TX, SEG, L>;
     static std::mutex mu;
     static std::map<size_t, int> occ;
@@ -153,15 +154,15 @@ cudaError_t launch_sweep_tma(int dir, TmaLaunch &P, const TmaGeom &g, int flags,
     P.nload = g.nload;
     P.sx = g.sx;
     if (dir == DIR_X) {
-        P.tiles_a = (ny - 2 + 7) / 8;
+        P.tiles_a = (ny - 2 + s.tx - 1) / s.tx;
         P.tiles_b = nz - 2;
-        P.tx_u = (uint32_t)(8 * g.sx * 4);
-        P.tx_m = (uint32_t)(8 * g.mwpr * 4);
+        P.tx_u = (uint32_t)(s.tx * g.sx * 4);
+        P.tx_m = (uint32_t)(s.tx * g.mwpr * 4);
     } else {
-        P.tiles_a = (nx - 1 + 31) / 32;
+        P.tiles_a = (nx - 1 + s.tx - 1) / s.tx;
         P.tiles_b = dir == DIR_Y ? nz - 2 : ny - 2;
-        P.tx_u = (uint32_t)(g.nload * g.rows * 32 * 4);
-        P.tx_m = (uint32_t)(g.nload * g.rows * 16);
+        P.tx_u = (uint32_t)(g.nload * g.rows * s.tx * 4);
+        P.tx_m = (uint32_t)(s.tx * g.mwpr * 4);
     }
 #define NPB_TMA_CASE_X(TX_, SEG_, L_)                                                        \
     if (dir == DIR_X && s.tx == TX_ && s.seg == SEG_ && s.len == L_)                         \
@@ -180,8 +181,12 @@ cudaError_t launch_sweep_tma(int dir, TmaLaunch &P, const TmaGeom &g, int flags,
 
 template <int DIR, int TX, int SEG, int L>
 static cudaError_t prepare_tma_shape() {
-    return cudaFuncSetAttribute(sweep_tma_kernel<DIR, TX, SEG, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                200 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(sweep_tma_kernel<DIR, TX, SEG, L>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sweep_tma_kernel<DIR, TX, SEG, L>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+    return e;
 }
 
 cudaError_t prepare_sweep_tma() {

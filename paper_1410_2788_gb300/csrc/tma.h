@@ -12,15 +12,23 @@ struct TmaGeom {
     bool ok;
     int rows, nload;      // y/z: rows per box, boxes per tile
     int sx, xc, nchunk;   // x: shared row stride = xc * nchunk
-    int mwpr;             // mask words per row
+    int mwpr;             // words per line of the line-major mask of this direction
 };
 
 TmaGeom tma_geometry(int dir, int nx, int ny, int nz, int pitch);
-bool tma_encode_state(CUtensorMap *m, void *u, int dir, const TmaGeom &g, int nx, int ny, int nz, int pitch);
-bool tma_encode_mask(CUtensorMap *m, const uint32_t *mask, int dir, const TmaGeom &g, int ny, int nz);
+bool tma_encode_state(CUtensorMap *m, void *u, int dir, const TmaGeom &g, int nx, int ny, int nz, int pitch,
+                      int tx);
+bool tma_encode_mask(CUtensorMap *m, const uint32_t *mask, int dir, const TmaGeom &g, int nx, int ny, int nz, int tx);
 cudaError_t launch_sweep_tma(int dir, TmaLaunch &P, const TmaGeom &g, int flags, SweepShape s, int sm_count,
                              cudaStream_t st);
 cudaError_t prepare_sweep_tma();
+
+// Lines per tile of the tensor-map variants: x sweeps 8; y/z sweeps 32 or 16.
+inline int tma_variant_tx(int dir, int v) { return dir == DIR_X ? 8 : (v == 0 ? 32 : 16); }
+inline int tma_variant(int dir, int tx) {
+    if (dir == DIR_X) return tx == 8 ? 0 : -1;
+    return tx == 32 ? 0 : (tx == 16 ? 1 : -1);
+}
 int tma_shapes(int dir, SweepShape *out, int max);
 
 }  // namespace npb

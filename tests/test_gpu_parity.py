@@ -290,3 +290,40 @@ def test_graph_replay_is_bitwise_stable(npb, ctx):
             assert a == b == c
     finally:
         npb.npb_grid_destroy(g)
+
+
+TMA_SHAPES = {0: [(8, 2, 17), (8, 4, 9), (8, 4, 17), (8, 8, 13), (8, 8, 17), (8, 16, 11), (8, 16, 17), (8, 32, 9)],
+              1: [(32, 2, 17), (32, 4, 9), (32, 4, 17), (32, 8, 13), (32, 8, 17), (32, 16, 11), (32, 16, 17),
+                  (16, 4, 17), (16, 8, 13), (16, 8, 17), (16, 16, 11), (16, 16, 17), (16, 32, 9)]}
+CLASSIC_SHAPES = [(16, 2, 17), (16, 4, 9), (16, 4, 17), (16, 8, 9), (16, 8, 13), (16, 8, 17), (16, 16, 9),
+                  (16, 16, 11), (16, 16, 17), (16, 32, 9), (32, 8, 17), (32, 16, 9)]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_every_solver_shape_matches_oracle(npb, O, prec):
+    """Each instantiated line-solver shape (Thomas/PCR split, lines per block, TMA pipeline or
+    not) gives the oracle's answer on a 65^3 molecule (RE+V, 6 steps)."""
+    p = I.random_walk_molecule(120, 65, 0.5, seed=I.SEED_BASE + 72)
+    n = 6
+    ref_dg, ref_legs, _ = O.energy(p, 10.0, n, return_legs=True)
+    tol = 1e-10 if prec == 0 else 1e-4
+    shapes = [(d, s) for d in range(3) for s in CLASSIC_SHAPES]
+    if prec == 1:
+        shapes += [(d, s) for d in range(3) for s in TMA_SHAPES[min(d, 1)]]
+    for d, (tx, seg, ln) in shapes:
+        if seg * ln < 65:
+            continue
+        c = npb.npb_ctx_create(0, 0)
+        try:
+            npb.npb_tune_set(c, prec, d, 65, tx, seg, ln)
+            assert npb.npb_tune_get(c, prec, d, 65) == (tx, seg, ln)
+            g = npb.npb_grid_create(c, p)
+            try:
+                dg = npb.npb_energy(g, npb.make_opts(0.4, 0.04, n, precision=prec))
+                u = npb.npb_potential(g, 1, npb.grid_shape(p))
+            finally:
+                npb.npb_grid_destroy(g)
+        finally:
+            npb.npb_ctx_destroy(c)
+        assert abs(dg - ref_dg) <= tol * abs(ref_dg), (d, tx, seg, ln, dg, ref_dg)
+        assert linf_rel(u, ref_legs["solvent_half"]) <= tol, (d, tx, seg, ln)
