@@ -280,15 +280,19 @@ static size_t state_bytes(const int n[3], int prec) {
 
 extern "C" size_t npb_grid_footprint(const npb_problem *p, int32_t precision) {
     if (!p) return 0;
-    const size_t pitch = (size_t)(p->n[0] + 31) / 32 * 32;
-    const size_t lines = (size_t)p->n[1] * p->n[2];
+    const size_t nx = p->n[0], ny = p->n[1], nz = p->n[2];
+    const size_t pitch = (nx + 31) / 32 * 32;
+    const size_t lines = ny * nz;
     const size_t na = p->n_atoms > 0 ? p->n_atoms : 0;
+    const size_t raw = std::max<size_t>(1, 8 * na);
     size_t b = 0;
-    b += 4 * state_bytes(p->n, precision);                       // four leg states
-    b += (size_t)mask_words_per_row((int)pitch) * lines * 4;     // node mask
-    b += 2 * lines * 4 + 8 * na * (4 + 8 + 8);                    // charge list
-    b += 4 * (size_t)face_count(p->n[0], p->n[1], p->n[2]) * 8;  // face data, 2 media x 2 kinds
-    b += na * 5 * 8 + 4096;                                       // atoms, result slot
+    b += 4 * state_bytes(p->n, precision);                                   // four leg states
+    b += (size_t)mask_words_per_row((int)pitch) * lines * 4;                 // node mask
+    b += nz * nx * line_words((int)ny) * 4 + ny * nx * line_words((int)nz) * 4;  // line-major masks
+    b += 2 * lines * 4 + raw * (4 + 8 + 8);                                  // charge list
+    b += 3 * lines * 4 + 2 * raw * sizeof(RawEntry) + 64;                    // its build scratch
+    b += 2 * (size_t)face_count(p->n[0], p->n[1], p->n[2]) * 8;              // face data, 2 media
+    b += na * 5 * 8 + 4 * sizeof(LegDev) + 4096;                             // atoms, legs, result
     return b;
 }
 
@@ -624,27 +628,34 @@ cudaError_t npb::launch_dir(npb_grid *g, int prec, int d, SweepShape shape, int 
     return launch_sweep(prec, d, g->d_legs[prec] + slot0, n_legs, nx, ny, nz, flags, shape, st);
 }
 
-// One LOD step for legs [slot0, slot0 + n_legs) of the leg table.  FP32 legs use the
-// TMA-pipelined sweeps where the grid's geometry allows it (the source stage then runs as its
-// own sparse launch); otherwise the one-tile-per-block sweeps with the source fused into x.
-int npb::run_step(npb_grid *g, int prec, int scheme, int slot0, int n_legs, cudaStream_t st) {
-    Profiler &pr = g->ctx->prof;
-    const LegDev *legs = g->d_legs[prec] + slot0;
-    const int nx = g->geo.nx, ny = g->geo.ny, nz = g->geo.nz;
+// One LOD step for an arbitrary list of legs of equal grid size, precision, scheme and eps
+// reading (possibly from different grids).  d_table holds their LegDev entries in the same order
+// (the one-tile-per-block kernels and the source stage read it).  FP32 legs use the
+// TMA-pipelined sweeps, in launches of up to kTmaMaxLegs legs, where every grid's geometry
+// allows it (the source stage then runs as its own sparse launch); otherwise the
+// one-tile-per-block sweeps with the source fused into x.
+int npb::step_legs(npb_ctx *ctx, const LegRef *refs, int n, const LegDev *d_table, int prec, int scheme,
+                   cudaStream_t st) {
+    if (n <= 0) return 0;
+    Profiler &pr = ctx->prof;
+    const GridGeom &geo = refs[0].g->geo;
+    const int nx = geo.nx, ny = geo.ny, nz = geo.nz;
     const int n_dir[3] = {nx, ny, nz};
     SweepShape shape[3];
     bool tma[3];
     for (int d = 0; d < 3; ++d) {
-        shape[d] = shape_for(g->ctx, prec, d, n_dir[d]);
-        tma[d] = shape[d].kind == 1 && prec == NPB_FP32_SWEEP && g->tma_ok[d] && n_legs <= kTmaMaxLegs &&
-                 g->h_legs[prec][slot0].eps_mode == 0;
+        shape[d] = shape_for(ctx, prec, d, n_dir[d]);
+        bool ok = shape[d].kind == 1 && prec == NPB_FP32_SWEEP;
+        for (int i = 0; i < n && ok; ++i)
+            ok = refs[i].g->tma_ok[d] && refs[i].g->h_legs[prec][refs[i].slot].eps_mode == 0;
+        tma[d] = ok && tma_variant(d, shape[d].tx) >= 0;
         if (shape[d].kind == 1 && !tma[d]) shape[d] = default_sweep_shape(prec, d, n_dir[d]);
     }
     cudaEvent_t ev{};
     int rc;
     if (scheme == NPB_LODIE2 && tma[0]) {
         if ((rc = pr.begin(st, &ev))) return rc;
-        CU(launch_source(prec, legs, n_legs, ny, nz, st));
+        CU(launch_source(prec, d_table, n, ny, nz, st));
         if ((rc = pr.end(st, ev, K_SOURCE))) return rc;
     }
     for (int d = 0; d < 3; ++d) {
@@ -652,15 +663,40 @@ int npb::run_step(npb_grid *g, int prec, int scheme, int slot0, int n_legs, cuda
         if (d == 0) flags = scheme == NPB_LODIE2 ? (tma[0] ? 0 : FUSE_PRE_SRC) : FUSE_PRE_NL;
         if (d == 2 && scheme == NPB_LODIE2) flags = FUSE_POST_NL;
         if ((rc = pr.begin(st, &ev))) return rc;
-        CU(launch_dir(g, prec, d, shape[d], slot0, n_legs, flags, st));
+        if (tma[d]) {
+            const int v = tma_variant(d, shape[d].tx);
+            for (int c0 = 0; c0 < n; c0 += kTmaMaxLegs) {
+                const int m = std::min(kTmaMaxLegs, n - c0);
+                TmaLaunch P;
+                memset(&P, 0, sizeof P);
+                for (int i = 0; i < m; ++i) {
+                    const LegRef &r = refs[c0 + i];
+                    P.umap[i] = r.g->tma_u[d][v][r.slot];
+                    P.mmap[i] = r.g->tma_m[d][v];
+                    P.legs[i] = r.g->h_legs[prec][r.slot];
+                }
+                P.n_legs = m;
+                P.err = refs[c0].g->d_err;
+                CU(launch_sweep_tma(d, P, refs[c0].g->tma_g[d], flags, shape[d], ctx->sm_count, st));
+            }
+        } else {
+            CU(launch_sweep(prec, d, d_table, n, nx, ny, nz, flags, shape[d], st));
+        }
         if ((rc = pr.end(st, ev, K_SWEEP_X + d))) return rc;
     }
     if (scheme == NPB_LODIE1) {
         if ((rc = pr.begin(st, &ev))) return rc;
-        CU(launch_source(prec, legs, n_legs, ny, nz, st));
+        CU(launch_source(prec, d_table, n, ny, nz, st));
         if ((rc = pr.end(st, ev, K_SOURCE))) return rc;
     }
     return 0;
+}
+
+// One LOD step for legs [slot0, slot0 + n_legs) of one grid's leg table.
+int npb::run_step(npb_grid *g, int prec, int scheme, int slot0, int n_legs, cudaStream_t st) {
+    LegRef refs[4];
+    for (int i = 0; i < n_legs; ++i) refs[i] = {g, slot0 + i};
+    return step_legs(g->ctx, refs, n_legs, g->d_legs[prec] + slot0, prec, scheme, st);
 }
 
 int npb::init_legs(npb_grid *g, int prec, const int *legs, int n, cudaStream_t st) {
@@ -704,6 +740,17 @@ int npb::enqueue_energy(npb_grid *g, const npb_opts *o, cudaStream_t st) {
     CU(launch_energy(prec, U[kLegSlot[0]], U[kLegSlot[1]], U[kLegSlot[2]], U[kLegSlot[3]],
                      g->d_ent_off, g->d_ent_qt, g->sc.total, re, g->d_result, st));
     if ((rc = g->ctx->prof.end(st, ev, K_ENERGY))) return rc;
+    CU(cudaMemcpyAsync(g->h_result, g->d_result, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(reinterpret_cast<int32_t *>(g->h_result + 1), g->d_err, sizeof(int32_t),
+                       cudaMemcpyDeviceToHost, st));
+    return 0;
+}
+
+// The RE+V energy of a grid whose legs have run, into its pinned result slot (no sync).
+int npb::enqueue_energy_reduce(npb_grid *g, int prec, int richardson, cudaStream_t st) {
+    void *const *U = g->d_u[prec];
+    CU(launch_energy(prec, U[kLegSlot[0]], U[kLegSlot[1]], U[kLegSlot[2]], U[kLegSlot[3]], g->d_ent_off,
+                     g->d_ent_qt, g->sc.total, richardson, g->d_result, st));
     CU(cudaMemcpyAsync(g->h_result, g->d_result, sizeof(double), cudaMemcpyDeviceToHost, st));
     CU(cudaMemcpyAsync(reinterpret_cast<int32_t *>(g->h_result + 1), g->d_err, sizeof(int32_t),
                        cudaMemcpyDeviceToHost, st));

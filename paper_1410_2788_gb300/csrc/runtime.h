@@ -134,7 +134,13 @@ int grid_states(Grid *g, int prec, cudaStream_t st);
 int grid_prepare(Grid *g, const npb_opts *o, cudaStream_t st);
 LegDev make_leg(const Grid *g, int leg, const npb_opts *o);
 SweepShape shape_for(Ctx *ctx, int prec, int dir, int n);
+struct LegRef {
+    Grid *g;
+    int slot;
+};
+int step_legs(Ctx *ctx, const LegRef *refs, int n, const LegDev *d_table, int prec, int scheme, cudaStream_t st);
 int run_step(Grid *g, int prec, int scheme, int slot0, int n_legs, cudaStream_t st);
+int enqueue_energy_reduce(Grid *g, int prec, int richardson, cudaStream_t st);
 int grid_tma(Grid *g);
 cudaError_t launch_dir(Grid *g, int prec, int d, SweepShape shape, int slot0, int n_legs, int flags, cudaStream_t st);
 int grid_check_err(Grid *g, cudaStream_t st, int host_copy);
