@@ -194,6 +194,68 @@ def cpu_baseline(problem, w, budget_s: float = 12.0):
             "sample": f"{reps} RE+V solve(s) of the same molecule with {n_s} steps per dt leg"}
 
 
+def serving_run(npb, seconds: float, rate: float = 50.0, fifo_requests: int = 12):
+    """Poisson arrivals (seeded stream of random-walk molecules, 100-20,000 atoms, h 0.25/0.5 A)
+    through npb_submit/npb_poll with continuous batching, FP32 sweeps; then the first
+    `fifo_requests` of the same stream through the plain FP64 single-solve path, one at a time
+    in arrival order, with the same arrival times."""
+    import threading
+
+    import numpy as np
+
+    import npb_inputs as I
+
+    count = max(1, int(round(seconds * rate)))
+    stream = list(I.serving_stream(count, rate_hz=rate))
+    o32 = npb.make_opts(DT, ALPHA, NSTEPS, precision=npb.NPB_FP32_SWEEP)
+    ctx = npb.npb_ctx_create(0, 0)
+    tickets = [None] * count
+    t0 = time.perf_counter()
+
+    def submitter():
+        for i, (ta, p) in enumerate(stream):
+            dt = t0 + ta - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            tickets[i] = npb.npb_submit(ctx, p, o32)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    th.join()
+    res = [npb.npb_poll(ctx, t, 600000) for t in tickets]
+    elapsed = time.perf_counter() - t0
+    npb.npb_ctx_destroy(ctx)
+    ok = [r for r in res if r.status == npb.NPB_OK]
+    lat = np.array([r.wall_ms for r in ok])
+    pts = sum(r.point_steps for r in ok)
+    out = {"requests": count, "completed": len(ok), "rate_hz": rate, "seconds": elapsed,
+           "solves_per_s": len(ok) / elapsed, "Mpoint_steps_per_s": pts / elapsed / 1e6,
+           "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
+           "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
+           "grids": sorted({int(r.n[0]) for r in ok}), "precision": "f32 sweeps, f64 energy"}
+    # the plain FP64 path, FIFO, on the first requests of the same stream
+    k = min(fifo_requests, count)
+    o64 = npb.make_opts(DT, ALPHA, NSTEPS, precision=npb.NPB_FP64)
+    ctx = npb.npb_ctx_create(0, 0)
+    lat64 = []
+    tf = time.perf_counter()
+    for i in range(k):
+        ta, p = stream[i]
+        now = time.perf_counter() - tf
+        if now < ta:
+            time.sleep(ta - now)
+        g = npb.npb_grid_create(ctx, p)
+        npb.npb_energy(g, o64)
+        npb.npb_grid_destroy(g)
+        lat64.append((time.perf_counter() - tf - ta) * 1e3)
+    el64 = time.perf_counter() - tf
+    npb.npb_ctx_destroy(ctx)
+    out["fp64_fifo"] = {"requests": k, "solves_per_s": k / el64, "p50_ms": float(np.percentile(lat64, 50)),
+                        "p99_ms": float(np.percentile(lat64, 99)),
+                        "note": "plain FP64 single-solve path, one request at a time in arrival order"}
+    return out
+
+
 def _kernel_source_hash() -> str:
     h = hashlib.sha256()
     for f in ("sweep_kernel.cuh", "sweep_launch.cuh"):
@@ -368,6 +430,7 @@ def run_ours(args):
             dist.destroy_process_group()
         return 0
     base = cpu_baseline(problem, w) if world == 1 else None
+    serving = serving_run(npb, args.serving_seconds) if (world == 1 and args.serving_seconds > 0) else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
@@ -389,6 +452,7 @@ def run_ours(args):
         "e2e": {"value": ue / te / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8,
                 "call": "npb_grid_create + npb_energy + npb_grid_destroy from pinned host arrays"},
         "gpu_launches": int(round(launches_per_step * args.steps)),
+        "serving": serving,
         "clocks": clk,
         "autotune": tuning[:0] if not args.verbose else tuning,
     }
@@ -408,6 +472,8 @@ def main(argv=None):
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--verbose", action="store_true")
+    ap.add_argument("--serving-seconds", type=float, default=5.0,
+                    help="length of the Poisson serving stream measured after the main line (0: skip)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3
