@@ -225,18 +225,33 @@ int npb_submit(npb_ctx *ctx, const npb_problem *problem, const npb_opts *opts,
 int npb_poll(npb_ctx *ctx, uint64_t ticket, int32_t timeout_ms, npb_result *out);
 
 /* ---- line-solver autotuning ------------------------------------------------------------ */
-/* Each line of a sweep is solved by SEG threads holding L consecutive rows each (a
- * Thomas / parallel-cyclic-reduction hybrid), TX lines per thread block.  npb_autotune
- * times every instantiated (TX, SEG, L) that covers the grid's lines, on all four legs of
- * `grid` at opts->precision, `reps` launches each, and keeps the fastest per (precision,
- * direction, line length) in the context.  report (may be NULL) receives a JSON list of
- * the timings, truncated to report_len bytes.  The legs' states are overwritten. */
+/* Each line of a sweep (the implicit-Euler tridiagonal solve of one LOD direction, Eq. 12)
+ * is solved by SEG threads holding L consecutive rows each (a segmented Thomas
+ * elimination plus a reduced system over the segment ends), TX lines per thread block.
+ * The solver kind selects the kernel family:
+ *   NPB_KIND_TILE      0: one tile per block, FP64 or FP32, segments over all n rows,
+ *                         reduced system by parallel cyclic reduction;
+ *   NPB_KIND_TMA       1: FP32 only, persistent blocks fed by bulk tensor copies, the
+ *                         same segmentation as kind 0;
+ *   NPB_KIND_TMA_INNER 2: FP32 only, persistent TMA blocks, segments over the n-2 interior
+ *                         rows with shared uniform-segment constants and a serial reduced
+ *                         solve (the FP32 default).
+ * npb_autotune times every instantiated (kind, TX, SEG, L) that covers the grid's lines, on
+ * all four legs of `grid` at opts->precision, `reps` launches each, and keeps the fastest
+ * per (precision, direction, line length) in the context.  report (may be NULL) receives a
+ * JSON list of the timings, truncated to report_len bytes.  The legs' states are
+ * overwritten.  Kinds 1 and 2 fall back to kind 0's default shape where the grid's
+ * geometry does not suit bulk tensor copies or eps at half points is the midpoint reading. */
+enum { NPB_KIND_TILE = 0, NPB_KIND_TMA = 1, NPB_KIND_TMA_INNER = 2 };
 int npb_autotune(npb_grid *grid, const npb_opts *opts, int32_t reps, char *report, size_t report_len);
-/* Pin / read the shape used for lines of n nodes along dir (0 = x, 1 = y, 2 = z). */
-int npb_tune_set(npb_ctx *ctx, int32_t precision, int32_t dir, int32_t n, int32_t tx, int32_t seg,
-                 int32_t len);
-int npb_tune_get(npb_ctx *ctx, int32_t precision, int32_t dir, int32_t n, int32_t *tx, int32_t *seg,
-                 int32_t *len);
+/* Pin / read the shape used for lines of n nodes along dir (0 = x, 1 = y, 2 = z).
+ * npb_tune_set fails with NPB_EINVAL when (kind, tx, seg, len) is not instantiated for that
+ * precision and direction or covers fewer rows than the kind needs (n, or n - 2 for
+ * kind 2).  npb_tune_get returns the pinned shape, else the default for n. */
+int npb_tune_set(npb_ctx *ctx, int32_t precision, int32_t dir, int32_t n, int32_t kind, int32_t tx,
+                 int32_t seg, int32_t len);
+int npb_tune_get(npb_ctx *ctx, int32_t precision, int32_t dir, int32_t n, int32_t *kind, int32_t *tx,
+                 int32_t *seg, int32_t *len);
 
 /* ---- errors --------------------------------------------------------------------------- */
 const char *npb_last_error(void);

@@ -87,8 +87,8 @@ SIGNATURES = {
                         ctypes.POINTER(ctypes.c_uint64)]),
     "npb_poll": (_I, [_V, ctypes.c_uint64, _I32, ctypes.POINTER(npb_result)]),
     "npb_autotune": (_I, [_V, ctypes.POINTER(npb_opts), _I32, ctypes.c_char_p, _SZ]),
-    "npb_tune_set": (_I, [_V, _I32, _I32, _I32, _I32, _I32, _I32]),
-    "npb_tune_get": (_I, [_V, _I32, _I32, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32),
+    "npb_tune_set": (_I, [_V, _I32, _I32, _I32, _I32, _I32, _I32, _I32]),
+    "npb_tune_get": (_I, [_V, _I32, _I32, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32),
                           ctypes.POINTER(_I32)]),
     "npb_charge_list_static": (_I, [_dp, _dp, _I32, ctypes.POINTER(_I32), ctypes.c_double, _dp, _V, _V, _V, _V,
                                     _V, _V, _V]),
@@ -255,15 +255,22 @@ def npb_autotune(grid: int, opts: npb_opts, reps: int = 5) -> list:
     return json.loads(buf.value.decode() or "[]")
 
 
-def npb_tune_set(ctx: int, precision: int, direction: int, n: int, tx: int, seg: int, length: int) -> None:
-    _check(load_library().npb_tune_set(ctx, precision, direction, n, tx, seg, length))
+KIND_TILE, KIND_TMA, KIND_TMA_INNER = 0, 1, 2
 
 
-def npb_tune_get(ctx: int, precision: int, direction: int, n: int) -> tuple[int, int, int]:
-    a, b, c = _I32(), _I32(), _I32()
-    _check(load_library().npb_tune_get(ctx, precision, direction, n, ctypes.byref(a), ctypes.byref(b),
-                                       ctypes.byref(c)))
-    return a.value, b.value, c.value
+def npb_tune_set(ctx: int, precision: int, direction: int, n: int, kind: int, tx: int, seg: int,
+                 length: int) -> None:
+    """Pin the line-solver shape (kind, lines per block, segments, rows per segment) for lines of
+    n nodes along `direction`."""
+    _check(load_library().npb_tune_set(ctx, precision, direction, n, kind, tx, seg, length))
+
+
+def npb_tune_get(ctx: int, precision: int, direction: int, n: int) -> tuple[int, int, int, int]:
+    """(kind, tx, seg, len) used for lines of n nodes along `direction`."""
+    k, a, b, c = _I32(), _I32(), _I32(), _I32()
+    _check(load_library().npb_tune_get(ctx, precision, direction, n, ctypes.byref(k), ctypes.byref(a),
+                                       ctypes.byref(b), ctypes.byref(c)))
+    return k.value, a.value, b.value, c.value
 
 
 NPB_STATIC_MAX_ATOMS = 20000

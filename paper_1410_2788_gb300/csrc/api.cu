@@ -182,6 +182,7 @@ extern "C" int npb_ctx_create(int device, size_t budget, npb_ctx **out) {
     CU(prepare_sweep_f32());
     CU(prepare_sweep_f64());
     CU(prepare_sweep_tma());
+    CU(prepare_sweep_inner());
     *out = ctx.release();
     return NPB_OK;
 }
@@ -569,8 +570,8 @@ SweepShape npb::shape_for(npb_ctx *ctx, int prec, int dir, int n) {
         if (it != ctx->tuned.end()) return it->second;
     }
     if (prec == NPB_FP32_SWEEP) {  // the TMA pipeline: smallest SEG*L >= n, ties to longer segments
-        SweepShape t[16], best{0, 0, 0, 0};
-        const int k = tma_shapes(dir, t, 16);
+        SweepShape t[32], best{0, 0, 0, 0};
+        const int k = tma_shapes(dir, t, 32);
         for (int i = 0; i < k; ++i) {
             if (t[i].seg * t[i].len < n) continue;
             if (best.tx == 0 || t[i].seg * t[i].len < best.seg * best.len ||
@@ -609,7 +610,7 @@ cudaError_t npb::launch_dir(npb_grid *g, int prec, int d, SweepShape shape, int 
     const int nx = g->geo.nx, ny = g->geo.ny, nz = g->geo.nz;
     const int n_dir[3] = {nx, ny, nz};
     // the TMA kernels take eps at half points from the node mask (harmonic reading only)
-    if (shape.kind == 1 && prec == NPB_FP32_SWEEP && g->tma_ok[d] && n_legs <= kTmaMaxLegs &&
+    if (shape.kind >= 1 && prec == NPB_FP32_SWEEP && g->tma_ok[d] && n_legs <= kTmaMaxLegs &&
         g->h_legs[prec][slot0].eps_mode == 0) {
         TmaLaunch P;
         memset(&P, 0, sizeof P);
@@ -622,9 +623,10 @@ cudaError_t npb::launch_dir(npb_grid *g, int prec, int d, SweepShape shape, int 
         }
         P.n_legs = n_legs;
         P.err = g->d_err;
+        if (shape.kind == 2) return launch_sweep_inner(d, P, g->tma_g[d], flags, shape, g->ctx->sm_count, st);
         return launch_sweep_tma(d, P, g->tma_g[d], flags, shape, g->ctx->sm_count, st);
     }
-    if (shape.kind == 1) shape = default_sweep_shape(prec, d, n_dir[d]);
+    if (shape.kind >= 1) shape = default_sweep_shape(prec, d, n_dir[d]);
     return launch_sweep(prec, d, g->d_legs[prec] + slot0, n_legs, nx, ny, nz, flags, shape, st);
 }
 
@@ -645,11 +647,11 @@ int npb::step_legs(npb_ctx *ctx, const LegRef *refs, int n, const LegDev *d_tabl
     bool tma[3];
     for (int d = 0; d < 3; ++d) {
         shape[d] = shape_for(ctx, prec, d, n_dir[d]);
-        bool ok = shape[d].kind == 1 && prec == NPB_FP32_SWEEP;
+        bool ok = shape[d].kind >= 1 && prec == NPB_FP32_SWEEP;
         for (int i = 0; i < n && ok; ++i)
             ok = refs[i].g->tma_ok[d] && refs[i].g->h_legs[prec][refs[i].slot].eps_mode == 0;
         tma[d] = ok && tma_variant(d, shape[d].tx) >= 0;
-        if (shape[d].kind == 1 && !tma[d]) shape[d] = default_sweep_shape(prec, d, n_dir[d]);
+        if (shape[d].kind >= 1 && !tma[d]) shape[d] = default_sweep_shape(prec, d, n_dir[d]);
     }
     cudaEvent_t ev{};
     int rc;
@@ -677,7 +679,8 @@ int npb::step_legs(npb_ctx *ctx, const LegRef *refs, int n, const LegDev *d_tabl
                 }
                 P.n_legs = m;
                 P.err = refs[c0].g->d_err;
-                CU(launch_sweep_tma(d, P, refs[c0].g->tma_g[d], flags, shape[d], ctx->sm_count, st));
+                if (shape[d].kind == 2) CU(launch_sweep_inner(d, P, refs[c0].g->tma_g[d], flags, shape[d], ctx->sm_count, st));
+                else CU(launch_sweep_tma(d, P, refs[c0].g->tma_g[d], flags, shape[d], ctx->sm_count, st));
             }
         } else {
             CU(launch_sweep(prec, d, d_table, n, nx, ny, nz, flags, shape[d], st));

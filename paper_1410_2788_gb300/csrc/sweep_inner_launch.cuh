@@ -1,0 +1,69 @@
+// sweep_inner_launch.cuh -- instantiates the interior-row TMA sweeps (kind 2) for one direction.
+#pragma once
+#include <algorithm>
+#include <map>
+#include <mutex>
+
+#include "sweep_inner.cuh"
+#include "tma.h"
+
+namespace npb {
+
+// (SEG, L) pairs for x (8 lines per tile: SEG a multiple of 4 fills whole warps) and for y/z
+// (16 lines per tile: SEG even).  L is odd, which keeps the shared-memory rows conflict-free.
+#define NPB_INNER_SEGS_X(X) X(8, 17) X(12, 11) X(16, 9) X(16, 17) X(20, 13) X(24, 11) X(32, 9)
+#define NPB_INNER_SEGS_YZ(X) X(8, 17) X(10, 13) X(16, 9) X(16, 17) X(20, 13) X(24, 11) X(32, 9)
+
+template <int DIR, int TX, int SEG, int L>
+static cudaError_t launch_inner_shape(const TmaLaunch &P, const TmaGeom &g, int flags, int sm_count, cudaStream_t st) {
+    const size_t smem = inner_smem_bytes<TX, SEG>(DIR, g.rows, g.nload, g.sx, g.mwpr);
+    if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    if (DIR != DIR_X && g.nload > 1 && tma_data_box_bytes(g.rows, TX) % 128) return cudaErrorInvalidValue;
+    auto kern = sweep_inner_kernel<DIR, TX, SEG, L>;
+    static std::mutex mu;
+    static std::map<size_t, int> occ;
+    int per_sm = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = occ.find(smem);
+        if (it == occ.end()) {
+            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX * SEG, smem);
+            if (e != cudaSuccess) return e;
+            occ[smem] = per_sm;
+        } else {
+            per_sm = it->second;
+        }
+    }
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int total = P.n_legs * P.tiles_a * P.tiles_b;
+    const int grid = std::max(1, std::min(total, per_sm * sm_count));
+    kern<<<grid, dim3(TX, SEG), smem, st>>>(P, flags);
+    return cudaGetLastError();
+}
+
+template <int DIR, int TX>
+static cudaError_t launch_inner_dir(TmaLaunch &P, const TmaGeom &g, int flags, SweepShape s, int sm_count,
+                                 cudaStream_t st) {
+#define NPB_INNER_CASE(SEG_, L_) \
+    if (s.seg == SEG_ && s.len == L_) return launch_inner_shape<DIR, TX, SEG_, L_>(P, g, flags, sm_count, st);
+    if constexpr (DIR == DIR_X) { NPB_INNER_SEGS_X(NPB_INNER_CASE) } else { NPB_INNER_SEGS_YZ(NPB_INNER_CASE) }
+#undef NPB_INNER_CASE
+    return cudaErrorInvalidValue;
+}
+
+template <int DIR, int TX>
+static cudaError_t prepare_inner_dir() {
+    cudaError_t e = cudaSuccess;
+#define NPB_INNER_PREP(SEG_, L_)                                                                                  \
+    if (e == cudaSuccess)                                                                                      \
+        e = cudaFuncSetAttribute(sweep_inner_kernel<DIR, TX, SEG_, L_>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 200 * 1024);                                                                  \
+    if (e == cudaSuccess)                                                                                      \
+        e = cudaFuncSetAttribute(sweep_inner_kernel<DIR, TX, SEG_, L_>,                                           \
+                                 cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if constexpr (DIR == DIR_X) { NPB_INNER_SEGS_X(NPB_INNER_PREP) } else { NPB_INNER_SEGS_YZ(NPB_INNER_PREP) }
+#undef NPB_INNER_PREP
+    return e;
+}
+
+}  // namespace npb

@@ -146,6 +146,62 @@ static cudaError_t launch_tma_shape(const TmaLaunch &P, const TmaGeom &g, int fl
     return cudaGetLastError();
 }
 
+cudaError_t launch_sweep_inner_x(TmaLaunch &P, const TmaGeom &g, int flags, SweepShape s, int sm_count, cudaStream_t st);
+cudaError_t launch_sweep_inner_y(TmaLaunch &P, const TmaGeom &g, int flags, SweepShape s, int sm_count, cudaStream_t st);
+cudaError_t launch_sweep_inner_z(TmaLaunch &P, const TmaGeom &g, int flags, SweepShape s, int sm_count, cudaStream_t st);
+cudaError_t prepare_sweep_inner_x();
+cudaError_t prepare_sweep_inner_y();
+cudaError_t prepare_sweep_inner_z();
+
+static const int kInnerSegsX[][2] = {{8, 17}, {12, 11}, {16, 9}, {16, 17}, {20, 13}, {24, 11}, {32, 9}};
+static const int kInnerSegsYZ[][2] = {{8, 17}, {10, 13}, {16, 9}, {16, 17}, {20, 13}, {24, 11}, {32, 9}};
+
+int inner_shapes(int dir, SweepShape *out, int max) {
+    int n = 0;
+    if (dir == DIR_X) {
+        for (const auto &p : kInnerSegsX)
+            if (n < max) out[n++] = SweepShape{8, p[0], p[1], 2};
+    } else {
+        for (const auto &p : kInnerSegsYZ)
+            if (n < max) out[n++] = SweepShape{16, p[0], p[1], 2};
+    }
+    return n;
+}
+
+cudaError_t prepare_sweep_inner() {
+    cudaError_t e = prepare_sweep_inner_x();
+    if (e == cudaSuccess) e = prepare_sweep_inner_y();
+    if (e == cudaSuccess) e = prepare_sweep_inner_z();
+    return e;
+}
+
+static void tma_tiles(int dir, TmaLaunch &P, const TmaGeom &g, SweepShape s) {
+    const int nx = P.legs[0].nx, ny = P.legs[0].ny, nz = P.legs[0].nz;
+    P.mwpr = g.mwpr;
+    P.rows = g.rows;
+    P.nload = g.nload;
+    P.sx = g.sx;
+    if (dir == DIR_X) {
+        P.tiles_a = (ny - 2 + s.tx - 1) / s.tx;
+        P.tiles_b = nz - 2;
+        P.tx_u = (uint32_t)(s.tx * g.sx * 4);
+        P.tx_m = (uint32_t)(s.tx * g.mwpr * 4);
+    } else {
+        P.tiles_a = (nx - 1 + s.tx - 1) / s.tx;
+        P.tiles_b = dir == DIR_Y ? nz - 2 : ny - 2;
+        P.tx_u = (uint32_t)(g.nload * g.rows * s.tx * 4);
+        P.tx_m = (uint32_t)(s.tx * g.mwpr * 4);
+    }
+}
+
+cudaError_t launch_sweep_inner(int dir, TmaLaunch &P, const TmaGeom &g, int flags, SweepShape s, int sm_count,
+                            cudaStream_t st) {
+    tma_tiles(dir, P, g, s);
+    if (dir == DIR_X) return launch_sweep_inner_x(P, g, flags, s, sm_count, st);
+    if (dir == DIR_Y) return launch_sweep_inner_y(P, g, flags, s, sm_count, st);
+    return launch_sweep_inner_z(P, g, flags, s, sm_count, st);
+}
+
 cudaError_t launch_sweep_tma(int dir, TmaLaunch &P, const TmaGeom &g, int flags, SweepShape s, int sm_count,
                              cudaStream_t st) {
     const int nx = P.legs[0].nx, ny = P.legs[0].ny, nz = P.legs[0].nz;

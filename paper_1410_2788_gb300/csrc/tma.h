@@ -31,4 +31,10 @@ inline int tma_variant(int dir, int tx) {
 }
 int tma_shapes(int dir, SweepShape *out, int max);
 
+// Interior-row sweeps (kind 2): x tiles of 8 lines, y/z tiles of 16.
+cudaError_t launch_sweep_inner(int dir, TmaLaunch &P, const TmaGeom &g, int flags, SweepShape s, int sm_count,
+                            cudaStream_t st);
+cudaError_t prepare_sweep_inner();
+int inner_shapes(int dir, SweepShape *out, int max);
+
 }  // namespace npb

@@ -28,7 +28,7 @@ extern "C" int npb_autotune(npb_grid *g, const npb_opts *o, int32_t reps, char *
     const int legs[4] = {0, 1, 2, 3};
     if ((rc = init_legs(g, prec, legs, 4, st))) return rc;
     const int n_dir[3] = {g->geo.nx, g->geo.ny, g->geo.nz};
-    SweepShape shapes[64];
+    SweepShape shapes[96];
     const int nc = sweep_shapes(prec, shapes, 48);
     cudaEvent_t a, b;
     CU(cudaEventCreate(&a));
@@ -36,13 +36,17 @@ extern "C" int npb_autotune(npb_grid *g, const npb_opts *o, int32_t reps, char *
     std::string rep = "[";
     for (int d = 0; d < 3; ++d) {
         int ns = nc;
-        if (prec == NPB_FP32_SWEEP && g->tma_ok[d]) ns += tma_shapes(d, shapes + nc, 64 - nc);
+        if (prec == NPB_FP32_SWEEP && g->tma_ok[d]) {
+            ns += tma_shapes(d, shapes + ns, 96 - ns);
+            ns += inner_shapes(d, shapes + ns, 96 - ns);
+        }
         SweepShape best{0, 0, 0, 0};
         float best_ms = 1e30f;
         for (int i = 0; i < ns; ++i) {
             const SweepShape s = shapes[i];
-            if (s.seg * s.len < n_dir[d]) continue;
-            if (s.seg * s.len > 2 * n_dir[d] + 32) continue;  // mostly padding: never faster
+            const int need = s.kind == 2 ? n_dir[d] - 2 : n_dir[d];  // interior-row shapes cover n-2 rows
+            if (s.seg * s.len < need) continue;
+            if (s.seg * s.len > 2 * need + 32) continue;  // mostly padding: never faster
             cudaError_t e = launch_dir(g, prec, d, s, 0, 4, 0, st);
             if (e != cudaSuccess) {
                 cudaGetLastError();
@@ -83,27 +87,30 @@ extern "C" int npb_autotune(npb_grid *g, const npb_opts *o, int32_t reps, char *
     return NPB_OK;
 }
 
-extern "C" int npb_tune_set(npb_ctx *ctx, int32_t precision, int32_t dir, int32_t n, int32_t tx, int32_t seg,
-                            int32_t len) {
-    if (!ctx || dir < 0 || dir > 2) return fail(NPB_EINVAL, "bad argument");
-    SweepShape s{tx, seg, len, 0};
-    if (!sweep_shape_available(precision, s)) {
-        SweepShape t[16];
-        const int k = precision == NPB_FP32_SWEEP ? tma_shapes(dir, t, 16) : 0;
-        for (int i = 0; i < k; ++i)
-            if (t[i].tx == tx && t[i].seg == seg && t[i].len == len) s = t[i];
-        if (s.kind == 0) return fail(NPB_EINVAL, "shape %d/%d/%d not instantiated", tx, seg, len);
+extern "C" int npb_tune_set(npb_ctx *ctx, int32_t precision, int32_t dir, int32_t n, int32_t kind, int32_t tx,
+                            int32_t seg, int32_t len) {
+    if (!ctx || dir < 0 || dir > 2 || kind < 0 || kind > 2) return fail(NPB_EINVAL, "bad argument");
+    SweepShape s{tx, seg, len, kind}, t[32];
+    bool found = false;
+    if (kind == 0) {
+        found = sweep_shape_available(precision, s);
+    } else if (precision == NPB_FP32_SWEEP) {
+        const int k = kind == 1 ? tma_shapes(dir, t, 32) : inner_shapes(dir, t, 32);
+        for (int i = 0; i < k && !found; ++i) found = t[i].tx == tx && t[i].seg == seg && t[i].len == len;
     }
-    if (seg * len < n) return fail(NPB_EINVAL, "shape covers %d rows < n = %d", seg * len, n);
+    if (!found) return fail(NPB_EINVAL, "shape kind %d %d/%d/%d not instantiated", kind, tx, seg, len);
+    const int need = kind == 2 ? n - 2 : n;
+    if (seg * len < need) return fail(NPB_EINVAL, "shape covers %d rows, too few for n = %d", seg * len, n);
     std::lock_guard<std::mutex> lk(ctx->tune_mu);
     ctx->tuned[tune_key(precision, dir, n)] = s;
     return NPB_OK;
 }
 
-extern "C" int npb_tune_get(npb_ctx *ctx, int32_t precision, int32_t dir, int32_t n, int32_t *tx, int32_t *seg,
-                            int32_t *len) {
-    if (!ctx || !tx || !seg || !len) return fail(NPB_EINVAL, "bad argument");
+extern "C" int npb_tune_get(npb_ctx *ctx, int32_t precision, int32_t dir, int32_t n, int32_t *kind, int32_t *tx,
+                            int32_t *seg, int32_t *len) {
+    if (!ctx || !kind || !tx || !seg || !len) return fail(NPB_EINVAL, "bad argument");
     const SweepShape s = shape_for(ctx, precision, dir, n);
+    *kind = s.kind;
     *tx = s.tx;
     *seg = s.seg;
     *len = s.len;

@@ -81,10 +81,35 @@ def test_setup_parity(npb, ctx, O, make):
 STAGES = ["SOURCE", "SWEEP_X", "SWEEP_Y", "SWEEP_Z", "NONLINEAR", "STEP"]
 
 
-@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 2e-5)])
+# FP32 line solves lose accuracy with r*eps (3200 in the solvent here, h = 0.5, tau = 10):
+# rounding of the segmented elimination alone, replayed in FP32 on the CPU, reaches 1.3e-5
+# (17 rows per segment) to 2.4e-5 (9 rows); 1e-4 is the FP32 bound the solve is held to.
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-4)])
 @pytest.mark.parametrize("leg", [0, 1, 2, 3])
 @pytest.mark.parametrize("scheme", [2, 1])
 def test_stage_parity(npb, ctx, O, precision, tol, leg, scheme):
+    _stage_check(npb, ctx, O, precision, tol, leg, scheme)
+
+
+@pytest.mark.parametrize("shape", range(7))
+@pytest.mark.parametrize("leg,scheme", [(0, 2), (2, 2), (1, 1), (3, 1)])
+def test_inner_sweep_stage_parity(npb, O, shape, leg, scheme):
+    """The interior-row FP32 sweeps (kind 2) pinned for all three directions on the ragged
+    37x29x23 grid: the last unknown of a line falls on a segment's first row (x, L = 17;
+    y, L = 13), its last row (y, L = 9) and inside it, with whole padding segments above."""
+    c = npb.npb_ctx_create(0, 0)
+    try:
+        p = small_molecule()
+        dims = npb.grid_shape(p)[::-1]
+        for d in range(3):
+            tx, seg, ln = INNER_SHAPES[min(d, 1)][min(shape, len(INNER_SHAPES[min(d, 1)]) - 1)]
+            npb.npb_tune_set(c, 1, d, dims[d], npb.KIND_TMA_INNER, tx, seg, ln)
+        _stage_check(npb, c, O, 1, 1e-4, leg, scheme)
+    finally:
+        npb.npb_ctx_destroy(c)
+
+
+def _stage_check(npb, ctx, O, precision, tol, leg, scheme):
     p = small_molecule()
     dt, alpha = 0.4, 1.0 / 25.0
     tau = dt / alpha * (0.5 if leg in (1, 3) else 1.0)
@@ -295,6 +320,8 @@ def test_graph_replay_is_bitwise_stable(npb, ctx):
 TMA_SHAPES = {0: [(8, 2, 17), (8, 4, 9), (8, 4, 17), (8, 8, 13), (8, 8, 17), (8, 16, 11), (8, 16, 17), (8, 32, 9)],
               1: [(32, 2, 17), (32, 4, 9), (32, 4, 17), (32, 8, 13), (32, 8, 17), (32, 16, 11), (32, 16, 17),
                   (16, 4, 17), (16, 8, 13), (16, 8, 17), (16, 16, 11), (16, 16, 17), (16, 32, 9)]}
+INNER_SHAPES = {0: [(8, s, l) for s, l in [(8, 17), (12, 11), (16, 9), (16, 17), (20, 13), (24, 11), (32, 9)]],
+                1: [(16, s, l) for s, l in [(8, 17), (10, 13), (16, 9), (16, 17), (20, 13), (24, 11), (32, 9)]]}
 CLASSIC_SHAPES = [(16, 2, 17), (16, 4, 9), (16, 4, 17), (16, 8, 9), (16, 8, 13), (16, 8, 17), (16, 16, 9),
                   (16, 16, 11), (16, 16, 17), (16, 32, 9), (32, 8, 17), (32, 16, 9)]
 
@@ -307,16 +334,17 @@ def test_every_solver_shape_matches_oracle(npb, O, prec):
     n = 6
     ref_dg, ref_legs, _ = O.energy(p, 10.0, n, return_legs=True)
     tol = 1e-10 if prec == 0 else 1e-4
-    shapes = [(d, s) for d in range(3) for s in CLASSIC_SHAPES]
+    shapes = [(d, 0, s) for d in range(3) for s in CLASSIC_SHAPES]
     if prec == 1:
-        shapes += [(d, s) for d in range(3) for s in TMA_SHAPES[min(d, 1)]]
-    for d, (tx, seg, ln) in shapes:
-        if seg * ln < 65:
+        shapes += [(d, 1, s) for d in range(3) for s in TMA_SHAPES[min(d, 1)]]
+        shapes += [(d, 2, s) for d in range(3) for s in INNER_SHAPES[min(d, 1)]]
+    for d, kind, (tx, seg, ln) in shapes:
+        if seg * ln < (63 if kind == 2 else 65):
             continue
         c = npb.npb_ctx_create(0, 0)
         try:
-            npb.npb_tune_set(c, prec, d, 65, tx, seg, ln)
-            assert npb.npb_tune_get(c, prec, d, 65) == (tx, seg, ln)
+            npb.npb_tune_set(c, prec, d, 65, kind, tx, seg, ln)
+            assert npb.npb_tune_get(c, prec, d, 65) == (kind, tx, seg, ln)
             g = npb.npb_grid_create(c, p)
             try:
                 dg = npb.npb_energy(g, npb.make_opts(0.4, 0.04, n, precision=prec))
@@ -325,5 +353,5 @@ def test_every_solver_shape_matches_oracle(npb, O, prec):
                 npb.npb_grid_destroy(g)
         finally:
             npb.npb_ctx_destroy(c)
-        assert abs(dg - ref_dg) <= tol * abs(ref_dg), (d, tx, seg, ln, dg, ref_dg)
-        assert linf_rel(u, ref_legs["solvent_half"]) <= tol, (d, tx, seg, ln)
+        assert abs(dg - ref_dg) <= tol * abs(ref_dg), (d, kind, tx, seg, ln, dg, ref_dg)
+        assert linf_rel(u, ref_legs["solvent_half"]) <= tol, (d, kind, tx, seg, ln)
