@@ -372,7 +372,9 @@ def run_ours(args):
     npb.npb_ctx_profile(ctx, False)
     mine = {k: v for k, v in stats.items() if v["launches"] > 0}
     launches_per_step = sum(v["launches"] for v in mine.values()) / kp
-    dom = max(mine, key=lambda k: mine[k]["ms"])
+    # the roofline is stated for the sweeps (the hot path); kernel_share lists every kernel
+    sweeps = [k for k in mine if k.startswith("sweep")]
+    dom = max(sweeps or mine, key=lambda k: mine[k]["ms"])
     nx, ny, nz = problem.n
     interior = (nx - 2) * (ny - 2) * (nz - 2)
     elem = 4 if prec == npb.NPB_FP32_SWEEP else 8

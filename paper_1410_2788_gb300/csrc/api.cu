@@ -290,7 +290,7 @@ extern "C" size_t npb_grid_footprint(const npb_problem *p, int32_t precision) {
     b += 4 * state_bytes(p->n, precision);                                   // four leg states
     b += (size_t)mask_words_per_row((int)pitch) * lines * 4;                 // node mask
     b += nz * nx * line_words((int)ny) * 4 + ny * nx * line_words((int)nz) * 4;  // line-major masks
-    b += 2 * lines * 4 + raw * (4 + 8 + 8);                                  // charge list
+    b += 2 * lines * 4 + raw * (4 + 8 + 8 + 8);                              // charge list
     b += 3 * lines * 4 + 2 * raw * sizeof(RawEntry) + 64;                    // its build scratch
     b += 2 * (size_t)face_count(p->n[0], p->n[1], p->n[2]) * 8;              // face data, 2 media
     b += na * 5 * 8 + 4 * sizeof(LegDev) + 4096;                             // atoms, legs, result
@@ -358,6 +358,7 @@ int npb::grid_build(npb_ctx *ctx, const npb_problem *p, cudaStream_t st, npb_gri
     if ((rc = galloc(g, &g->d_ent_x, n_raw))) return guard(rc);
     if ((rc = galloc(g, &g->d_ent_qt, n_raw))) return guard(rc);
     if ((rc = galloc(g, &g->d_ent_off, n_raw))) return guard(rc);
+    if ((rc = galloc(g, &g->d_ent_xq, n_raw))) return guard(rc);
     if ((rc = galloc(g, &g->d_result, 8))) return guard(rc);
     if ((rc = galloc(g, &g->d_err, 4))) return guard(rc);
     CU(cudaMemsetAsync(g->d_err, 0, 4 * sizeof(int32_t), st));
@@ -413,7 +414,7 @@ int npb::grid_setup(npb_grid *g, cudaStream_t st) {
     if ((rc = pr.end(st, ev, K_SETUP_MASK))) return rc;
     if ((rc = pr.begin(st, &ev))) return rc;
     CU(setup_charges(g->geo, g->d_xyz, g->d_q, na, g->sc, g->d_line_begin, g->d_line_count, g->d_ent_x,
-                     g->d_ent_qt, g->d_ent_off, st));
+                     g->d_ent_qt, g->d_ent_off, g->d_ent_xq, st));
     if ((rc = pr.end(st, ev, K_SETUP_CHARGES))) return rc;
     // face data are recomputed on their next use, only for the precision that uses them
     for (int m = 0; m < 2; ++m)
@@ -439,6 +440,18 @@ extern "C" void npb_grid_destroy(npb_grid *g) { grid_free(g); }
 int npb::grid_boundary(npb_grid *g, int medium, int prec, cudaStream_t st, const double **out) {
     const int kind = prec == NPB_FP64 ? 0 : 1;
     double *&bc = g->d_bc[medium][kind];
+    if (kind == 1 && (!bc || !g->bc_valid[medium][kind])) {  // FP32 pairs: both media in one pass
+        const int64_t nf = face_count(g->geo.nx, g->geo.ny, g->geo.nz);
+        int rc;
+        for (int m = 0; m < 2; ++m)
+            if (!g->d_bc[m][1] && (rc = galloc(g, &g->d_bc[m][1], (size_t)nf))) return rc;
+        g->bc_valid[NPB_SOLVENT][1] = g->bc_valid[NPB_VACUUM][1] = true;
+        cudaEvent_t ev{};
+        if ((rc = g->ctx->prof.begin(st, &ev))) return rc;
+        CU(setup_boundary_pair(g->geo, g->d_xyz, g->d_q, g->n_atoms, g->eps_out, std::sqrt(g->kappa2), g->eps_in,
+                               g->d_bc[NPB_SOLVENT][1], g->d_bc[NPB_VACUUM][1], st));
+        if ((rc = g->ctx->prof.end(st, ev, K_SETUP_BOUNDARY))) return rc;
+    }
     if (!bc || !g->bc_valid[medium][kind]) {
         int rc;
         if (!bc) {
@@ -510,6 +523,7 @@ LegDev npb::make_leg(const npb_grid *g, int leg, const npb_opts *o) {
     L.line_count = g->d_line_count;
     L.ent_x = g->d_ent_x;
     L.ent_qt = g->d_ent_qt;
+    L.ent_xq = g->d_ent_xq;
     L.src = tau * 4.0 * kPi * kBjerrum / (h * h * h);
     L.eps_mode = o->eps_mode == NPB_EPS_MIDPOINT ? 1 : 0;
     if (solvent) {
@@ -530,6 +544,10 @@ LegDev npb::make_leg(const npb_grid *g, int leg, const npb_opts *o) {
         L.nl_q = 1.0;
         L.nl_omq = 0.0;
     }
+    for (int i = 0; i < 3; ++i) L.rEf[i] = (float)L.rE[i];
+    L.nl_qf = (float)L.nl_q;
+    L.nl_omqf = (float)L.nl_omq;
+    L.srcf = (float)L.src;
     return L;
 }
 
@@ -569,14 +587,15 @@ SweepShape npb::shape_for(npb_ctx *ctx, int prec, int dir, int n) {
         auto it = ctx->tuned.find(tune_key(prec, dir, n));
         if (it != ctx->tuned.end()) return it->second;
     }
-    if (prec == NPB_FP32_SWEEP) {  // the TMA pipeline: smallest SEG*L >= n, ties to longer segments
+    if (prec == NPB_FP32_SWEEP) {
+        // interior-row TMA sweeps: rows solved (padding included) plus about eight rows' worth of
+        // work per segment for the reduced system; the cheapest shape covering the n-2 unknowns
         SweepShape t[32], best{0, 0, 0, 0};
-        const int k = tma_shapes(dir, t, 32);
+        const int k = inner_shapes(dir, t, 32);
+        auto cost = [](const SweepShape &s) { return s.seg * s.len + 8 * s.seg; };
         for (int i = 0; i < k; ++i) {
-            if (t[i].seg * t[i].len < n) continue;
-            if (best.tx == 0 || t[i].seg * t[i].len < best.seg * best.len ||
-                (t[i].seg * t[i].len == best.seg * best.len && t[i].len > best.len))
-                best = t[i];
+            if (t[i].seg * t[i].len < n - 2) continue;
+            if (best.tx == 0 || cost(t[i]) < cost(best)) best = t[i];
         }
         if (best.tx) return best;
     }
@@ -592,7 +611,7 @@ int npb::grid_tma(npb_grid *g) {
         g->tma_g[d] = tma_geometry(d, nx, ny, nz, pitch);
         bool ok = g->tma_g[d].ok && g->d_u[NPB_FP32_SWEEP][0] != nullptr;
         const uint32_t *lm = d == 0 ? g->d_mask : (d == 1 ? g->d_mask_y : g->d_mask_z);
-        for (int v = 0; v < 2 && ok; ++v) {  // x: 8 lines per tile; y/z: 32 or 16
+        for (int v = 0; v < tma_variant_count(d) && ok; ++v) {  // x: 8 lines per tile; y/z: 32, 16 or 8
             for (int s = 0; s < 4 && ok; ++s)
                 ok = tma_encode_state(&g->tma_u[d][v][s], g->d_u[NPB_FP32_SWEEP][s], d, g->tma_g[d], nx, ny, nz,
                                       pitch, tma_variant_tx(d, v));
@@ -634,8 +653,8 @@ cudaError_t npb::launch_dir(npb_grid *g, int prec, int d, SweepShape shape, int 
 // reading (possibly from different grids).  d_table holds their LegDev entries in the same order
 // (the one-tile-per-block kernels and the source stage read it).  FP32 legs use the
 // TMA-pipelined sweeps, in launches of up to kTmaMaxLegs legs, where every grid's geometry
-// allows it (the source stage then runs as its own sparse launch); otherwise the
-// one-tile-per-block sweeps with the source fused into x.
+// allows it; otherwise the one-tile-per-block sweeps.  The source stage is fused into the x
+// sweep except with the kind-1 TMA kernel, which leaves it to its own sparse launch.
 int npb::step_legs(npb_ctx *ctx, const LegRef *refs, int n, const LegDev *d_table, int prec, int scheme,
                    cudaStream_t st) {
     if (n <= 0) return 0;
@@ -655,14 +674,16 @@ int npb::step_legs(npb_ctx *ctx, const LegRef *refs, int n, const LegDev *d_tabl
     }
     cudaEvent_t ev{};
     int rc;
-    if (scheme == NPB_LODIE2 && tma[0]) {
+    // LODIE2's source stage: fused into the x sweep's load except by the kind-1 TMA kernel
+    const bool src_apart = scheme == NPB_LODIE2 && tma[0] && shape[0].kind == 1;
+    if (src_apart) {
         if ((rc = pr.begin(st, &ev))) return rc;
         CU(launch_source(prec, d_table, n, ny, nz, st));
         if ((rc = pr.end(st, ev, K_SOURCE))) return rc;
     }
     for (int d = 0; d < 3; ++d) {
         int flags = 0;
-        if (d == 0) flags = scheme == NPB_LODIE2 ? (tma[0] ? 0 : FUSE_PRE_SRC) : FUSE_PRE_NL;
+        if (d == 0) flags = scheme == NPB_LODIE2 ? (src_apart ? 0 : FUSE_PRE_SRC) : FUSE_PRE_NL;
         if (d == 2 && scheme == NPB_LODIE2) flags = FUSE_POST_NL;
         if ((rc = pr.begin(st, &ev))) return rc;
         if (tma[d]) {

@@ -51,6 +51,8 @@ struct LegDev {
     double nl_omq;             // 1 - nl_q, as -expm1(-kbar^2 tau)
     int32_t nl_on;             // 1: solvent nodes get the nonlinear stage
     int32_t eps_mode;          // 0 harmonic, 1 midpoint
+    float rEf[3], nl_qf, nl_omqf, srcf;  // the same constants rounded once to FP32 (FP32 sweeps)
+    const int2 *ent_xq;                  // charge entries as (x, FP32 qtilde), same order as ent_x
 };
 
 // Stage flags for the sweep kernels.

@@ -96,6 +96,7 @@ struct npb_grid {
     uint32_t *d_half[3] = {nullptr, nullptr, nullptr};
     int32_t *d_line_begin = nullptr, *d_line_count = nullptr, *d_ent_x = nullptr;
     double *d_ent_qt = nullptr;
+    int2 *d_ent_xq = nullptr;  // (x, FP32 qtilde) of each entry, for the FP32 sweeps' fused source
     int64_t *d_ent_off = nullptr;
     int n_ent = 0;
     double *d_bc[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [medium][0 fp64 | 1 fp32 pairs]
@@ -108,8 +109,8 @@ struct npb_grid {
     double *d_result = nullptr;
     double *h_result = nullptr;  // pinned
     int32_t *d_err = nullptr;    // set by a device wait that expired
-    CUtensorMap tma_u[3][2][4];  // FP32 leg states by [direction][lines-per-tile variant][slot]
-    CUtensorMap tma_m[3][2];     // line-major mask by [direction][variant]
+    CUtensorMap tma_u[3][3][4];  // FP32 leg states by [direction][lines-per-tile variant][slot]
+    CUtensorMap tma_m[3][3];     // line-major mask by [direction][variant]
     npb::TmaGeom tma_g[3] = {};
     bool tma_ok[3] = {false, false, false};
     bool tma_built = false;

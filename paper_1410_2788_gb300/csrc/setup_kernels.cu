@@ -173,7 +173,8 @@ __global__ void k_charge_merge(RawEntry *__restrict__ bucket, const int32_t *__r
 __global__ void k_charge_compact(GridGeom g, const RawEntry *__restrict__ bucket,
                                  const int32_t *__restrict__ raw_begin, const int32_t *__restrict__ begin,
                                  const int32_t *__restrict__ count, int32_t *__restrict__ ent_x,
-                                 double *__restrict__ ent_qt, int64_t *__restrict__ ent_off, int n_lines) {
+                                 double *__restrict__ ent_qt, int64_t *__restrict__ ent_off,
+                                 int2 *__restrict__ ent_xq, int n_lines) {
     const int ln = blockIdx.x * blockDim.x + threadIdx.x;
     if (ln >= n_lines) return;
     const int rb = raw_begin[ln], b = begin[ln], c = count[ln];
@@ -183,6 +184,7 @@ __global__ void k_charge_compact(GridGeom g, const RawEntry *__restrict__ bucket
         ent_x[b + i] = r.x;
         ent_qt[b + i] = r.val;
         ent_off[b + i] = ((int64_t)z * g.ny + y) * g.pitch + r.x;
+        if (ent_xq) ent_xq[b + i] = make_int2(r.x, __float_as_int((float)r.val));
     }
 }
 
@@ -289,6 +291,91 @@ __global__ void k_boundary_f32(GridGeom g, const double *__restrict__ xyz, const
     if (f < nf) out[f] = kBjerrum * (double)ieps * s;
 }
 
+// Both media's faces in one pass, FP32 pair terms (chunk sums in FP32, chunks accumulated in
+// FP64): solvent C sum q exp(-kbar d / sqrt(eps_out)) / (eps_out d), vacuum C sum q / (eps_in d).
+// The two share the distance and its reciprocal square root; each thread holds kFaceBlock face
+// nodes, so every atom read from shared memory serves several nodes.
+constexpr int kFaceBlock = 4;
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__global__ void k_boundary_pair_f32(GridGeom g, const double *__restrict__ xyz, const double *__restrict__ q,
+                                    int n_atoms, double eps_s, double kbar, double eps_v,
+                                    double *__restrict__ out_s, double *__restrict__ out_v) {
+    __shared__ float4 sa[kAtomChunk];
+    const int64_t nf = face_count(g.nx, g.ny, g.nz);
+    const int64_t f0 = (int64_t)blockIdx.x * blockDim.x * kFaceBlock + threadIdx.x;
+    float x[kFaceBlock], y[kFaceBlock], z[kFaceBlock];
+#pragma unroll
+    for (int r = 0; r < kFaceBlock; ++r) {
+        int i = 0, j = 0, k = 0;
+        const int64_t f = f0 + (int64_t)r * blockDim.x;
+        if (f < nf) face_node(f, g.nx, g.ny, g.nz, i, j, k);
+        // positions relative to the grid origin keep FP32 resolution near 1e-5 A
+        x[r] = (float)(i * g.h);
+        y[r] = (float)(j * g.h);
+        z[r] = (float)(k * g.h);
+    }
+    const float c = (float)(-kbar / sqrt(eps_s) * 1.4426950408889634);  // -kbar/sqrt(eps) * log2(e)
+    const bool coulomb = kbar == 0.0;
+    double ss[kFaceBlock], sv[kFaceBlock];
+#pragma unroll
+    for (int r = 0; r < kFaceBlock; ++r) ss[r] = sv[r] = 0.0;
+    for (int a0 = 0; a0 < n_atoms; a0 += kAtomChunk) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < kAtomChunk && a0 + t < n_atoms; t += blockDim.x)
+            sa[t] = make_float4((float)(xyz[3 * (a0 + t)] - g.ox), (float)(xyz[3 * (a0 + t) + 1] - g.oy),
+                                (float)(xyz[3 * (a0 + t) + 2] - g.oz), (float)q[a0 + t]);
+        __syncthreads();
+        const int na = min(kAtomChunk, n_atoms - a0);
+        float ps[kFaceBlock], pv[kFaceBlock];
+#pragma unroll
+        for (int r = 0; r < kFaceBlock; ++r) ps[r] = pv[r] = 0.f;
+        if (coulomb) {
+            for (int t = 0; t < na; ++t) {
+                const float4 A = sa[t];
+#pragma unroll
+                for (int r = 0; r < kFaceBlock; ++r) {
+                    const float dx = x[r] - A.x, dy = y[r] - A.y, dz = z[r] - A.z;
+                    pv[r] = fmaf(A.w, rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))), pv[r]);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < kFaceBlock; ++r) ps[r] = pv[r];
+        } else {
+            for (int t = 0; t < na; ++t) {
+                const float4 A = sa[t];
+#pragma unroll
+                for (int r = 0; r < kFaceBlock; ++r) {
+                    const float dx = x[r] - A.x, dy = y[r] - A.y, dz = z[r] - A.z;
+                    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    const float id = rsqrtf(d2);
+                    const float qi = A.w * id;
+                    pv[r] += qi;
+                    ps[r] = fmaf(qi, ex2_approx(c * (d2 * id)), ps[r]);
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kFaceBlock; ++r) {
+            ss[r] += (double)ps[r];
+            sv[r] += (double)pv[r];
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < kFaceBlock; ++r) {
+        const int64_t f = f0 + (int64_t)r * blockDim.x;
+        if (f < nf) {
+            out_s[f] = kBjerrum / eps_s * ss[r];
+            out_v[f] = kBjerrum / eps_v * sv[r];
+        }
+    }
+}
+
 // Zero interior, Dirichlet faces, zero padding: the initial state of a leg (Sec. 2.2).
 template <typename T>
 __global__ void k_init_leg(GridGeom g, const double *__restrict__ bc, T *__restrict__ u) {
@@ -370,7 +457,7 @@ cudaError_t setup_mask(const GridGeom &g, const double *xyz, const double *radiu
 
 cudaError_t setup_charges(const GridGeom &g, const double *xyz, const double *q, int n_atoms,
                           ChargeScratch &s, int32_t *line_begin, int32_t *line_count, int32_t *ent_x,
-                          double *ent_qt, int64_t *ent_off, cudaStream_t st) {
+                          double *ent_qt, int64_t *ent_off, int2 *ent_xq, cudaStream_t st) {
     const int n_lines = g.ny * g.nz;
     const int n_raw = 8 * n_atoms;
     cudaMemsetAsync(s.count, 0, sizeof(int32_t) * n_lines, st);
@@ -383,7 +470,7 @@ cudaError_t setup_charges(const GridGeom &g, const double *xyz, const double *q,
                                                              n_lines);
     k_scan_lines<<<1, 1024, 0, st>>>(line_count, line_begin, n_lines, s.total);
     k_charge_compact<<<blocks_for(n_lines, 128), 128, 0, st>>>(g, s.bucket, s.raw_begin, line_begin, line_count,
-                                                               ent_x, ent_qt, ent_off, n_lines);
+                                                               ent_x, ent_qt, ent_off, ent_xq, n_lines);
     return cudaGetLastError();
 }
 
@@ -393,6 +480,15 @@ cudaError_t setup_boundary(const GridGeom &g, const double *xyz, const double *q
     const int t = 128;
     if (fp32_pairs) k_boundary_f32<<<blocks_for(nf, t), t, 0, st>>>(g, xyz, q, n_atoms, eps, kbar, out);
     else k_boundary_f64<<<blocks_for(nf, t), t, 0, st>>>(g, xyz, q, n_atoms, eps, kbar, out);
+    return cudaGetLastError();
+}
+
+cudaError_t setup_boundary_pair(const GridGeom &g, const double *xyz, const double *q, int n_atoms, double eps_out,
+                                double kbar, double eps_in, double *out_s, double *out_v, cudaStream_t st) {
+    const int64_t nf = face_count(g.nx, g.ny, g.nz);
+    const int t = 128;
+    k_boundary_pair_f32<<<blocks_for(nf, (int64_t)t * kFaceBlock), t, 0, st>>>(g, xyz, q, n_atoms, eps_out, kbar,
+                                                                               eps_in, out_s, out_v);
     return cudaGetLastError();
 }
 

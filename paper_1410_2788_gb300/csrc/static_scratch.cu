@@ -109,7 +109,7 @@ extern "C" int npb_charge_list_static(const double *xyz, const double *q, int32_
     geo.oy = origin[1];
     geo.oz = origin[2];
     // setup_charges clears the per-line counters it accumulates into before using them
-    e = setup_charges(geo, s_xyz, s_q, n_atoms, sc, d_line_begin, d_line_count, d_ent_x, d_ent_qt, d_ent_off, st);
+    e = setup_charges(geo, s_xyz, s_q, n_atoms, sc, d_line_begin, d_line_count, d_ent_x, d_ent_qt, d_ent_off, nullptr, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_n_entries, sc.total, sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return fail(NPB_ECUDA, "static charge-list build failed: %s", cudaGetErrorString(e));

@@ -18,6 +18,8 @@
 //     face term eps u_{n-1} is moved to its right-hand side before the solve;
 //   * u_0 enters through the first row of segment 0 in the reduced system.
 #pragma once
+#include <type_traits>
+
 #include "sweep_tma.cuh"
 
 namespace npb {
@@ -42,7 +44,7 @@ __host__ __device__ __forceinline__ size_t inner_smem_bytes(int dir, int rows, i
     const size_t data = dir == DIR_X ? (size_t)TX * sx * 4 : (size_t)nload * tma_data_box_bytes(rows, TX);
     const size_t mask = (size_t)TX * mwpr * 4;
     const size_t red = (size_t)(TX * SEG + 2 * pcr_rows<TX, SEG>()) * 16 + (size_t)TX * SEG * 4;
-    return 128 + 2 * (tma_align(data) + tma_align(mask)) + tma_align(red) + 64;
+    return 128 + 2 * (tma_align(data) + tma_align(mask)) + tma_align(red) + 64;  // + barriers, tile indices
 }
 
 // The segment ends of one line: segment s contributes its F row (fa E_{s-1} + fb F_s + fc E_s = fd)
@@ -114,23 +116,18 @@ __global__ void __launch_bounds__(TX *SEG, (768 / (TX * SEG)) > 0 ? 768 / (TX * 
     float *ebuf = reinterpret_cast<float *>(fbuf + TX * SEG + 2 * kRows);
     off += tma_align((size_t)(TX * SEG + 2 * kRows) * 16 + (size_t)TX * SEG * 4);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + off);
+    int4 *tinfo = reinterpret_cast<int4 *>(bar + 2);  // (leg, a, b) of the tile in each stage
     for (int i = tid; i < 2 * kRows; i += TX * SEG) {  // identity rows; the margins are never written again
         fbuf[TX * SEG + i] = make_float4(0.f, 1.f, 0.f, 0.f);
     }
     auto at = [&](int g) -> int { return DIR == DIR_X ? line * P.sx + g : g * TX + line; };
 
-    if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-
     const int tpl = P.tiles_a * P.tiles_b;
     const int total = P.n_legs * tpl;
 
-    auto issue = [&](int t, int s) {  // thread 0 only
-        const int leg = t / tpl, r = t - leg * tpl, a = r % P.tiles_a, b = r / P.tiles_a;
+    auto issue = [&](int t, int s) {  // thread 0 only; the other threads read the tile's indices
+        const int leg = t / tpl, r = t - leg * tpl, b = r / P.tiles_a, a = r - b * P.tiles_a;
+        tinfo[s] = make_int4(leg, a, b, 0);
         const bool has_mask = P.legs[leg].mask != nullptr;
         mbar_expect_tx(&bar[s], P.tx_u + (has_mask ? P.tx_m : 0u));
         if (DIR == DIR_X) {
@@ -149,10 +146,29 @@ __global__ void __launch_bounds__(TX *SEG, (768 / (TX * SEG)) > 0 ? 768 / (TX * 
     };
 
     int t = blockIdx.x, it = 0;
-    if (tid == 0 && t < total) issue(t, 0);
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+        if (t < total) issue(t, 0);
+    }
+    __syncthreads();  // barriers initialised, the first tile's indices visible
     for (; t < total; t += gridDim.x, ++it) {
         const int s = it & 1;
         const int tn = t + gridDim.x;
+        // the tile's indices were written before the last block barrier: start the charge-list
+        // reads of the fused source stage now, under the wait for the tile's data
+        int e0 = 0, ne = 0;
+        if (DIR == DIR_X && (flags & FUSE_PRE_SRC)) {
+            const int4 ti = tinfo[s];
+            const LegDev &lg = P.legs[ti.x];
+            const int yl = 1 + ti.y * TX + line;
+            if (yl <= lg.ny - 2) {
+                const int ln = (1 + ti.z) * lg.ny + yl;
+                e0 = lg.line_begin[ln];
+                ne = lg.line_count[ln];
+            }
+        }
         if (tid == 0 && tn < total) {
             bulk_wait_read_all();
             issue(tn, s ^ 1);
@@ -167,11 +183,12 @@ __global__ void __launch_bounds__(TX *SEG, (768 / (TX * SEG)) > 0 ? 768 / (TX * 
             return;
         }
 
-        const int leg = t / tpl, rr = t - leg * tpl, a = rr % P.tiles_a, bb = rr / P.tiles_a;
+        const int4 ti = tinfo[s];
+        const int leg = ti.x, a = ti.y, bb = ti.z;
         const LegDev &lg = P.legs[leg];
         const int ndir = DIR == DIR_X ? lg.nx : (DIR == DIR_Y ? lg.ny : lg.nz);
-        const T rE0 = (T)lg.rE[0], rE1 = (T)lg.rE[1], rE2 = (T)lg.rE[2];
-        const T nlq = (T)lg.nl_q, nlomq = (T)lg.nl_omq;
+        const T rE0 = lg.rEf[0], rE1 = lg.rEf[1], rE2 = lg.rEf[2];
+        const T nlq = lg.nl_qf, nlomq = lg.nl_omqf;
         const bool nl_on = lg.nl_on != 0;
         const bool pre_nl = (flags & FUSE_PRE_NL) && nl_on;
         const bool post_nl = (flags & FUSE_POST_NL) && nl_on;
@@ -191,6 +208,15 @@ __global__ void __launch_bounds__(TX *SEG, (768 / (TX * SEG)) > 0 ? 768 / (TX * 
         // nodes that take the nonlinear flow: unknowns outside the molecule
         uint32_t flow = ~(nb >> 1) & (nrem >= 32 ? 0xffffffffu : (nrem > 0 ? (1u << nrem) - 1u : 0u));
 
+        // LODIE2 stage S fused into the x sweep: tau Q at this thread's own charge nodes (each
+        // thread scans its line's charge list, so no other thread's rows are touched)
+        if (DIR == DIR_X && (flags & FUSE_PRE_SRC)) {
+            for (int e = e0; e < e0 + ne; ++e) {
+                const int2 v = lg.ent_xq[e];
+                const int k = v.x - g0;
+                if (k >= 0 && k < L && k < nrem) D[at(v.x)] += lg.srcf * __int_as_float(v.y);
+            }
+        }
         // row n-2 of the line: move its face coupling eps u_{n-1} to the right-hand side (after
         // the inflowing nonlinear stage, so the flow sees the bare node value)
         if (nrem >= 1 && nrem <= L) {
@@ -203,50 +229,58 @@ __global__ void __launch_bounds__(TX *SEG, (768 / (TX * SEG)) > 0 ? 768 / (TX * 
         }
 
         T al[L], be[L], ga[L];
+        T fa, fb, fc, fd, ea, eb, ec, ed;
+        // The local elimination; FULL: every row of the segment is an unknown (no padding rows, no
+        // cut coupling below the E row), so the per-row guards drop out.
+        auto local = [&](auto full_tag) {
+            constexpr bool FULL = decltype(full_tag)::value;
 #pragma unroll
-        for (int k = 0; k < L; ++k) al[k] = k < nrem ? D[at(g0 + k)] : T(0);
-        if (pre_nl) {  // uniform over the tile: the flow code is not issued for other sweeps
+            for (int k = 0; k < L; ++k) al[k] = (FULL || k < nrem) ? D[at(g0 + k)] : T(0);
+            if (pre_nl) {  // uniform over the tile: the flow code is not issued for other sweeps
 #pragma unroll
-            for (int k = 0; k < L; ++k)
-                if ((flow >> k) & 1u) al[k] = nl_flow(al[k], nlq, nlomq);
-        }
-
-        // row 0 (F) coefficients, then the forward elimination over rows 1 .. L-2 with x_0 = F
-        const T em0 = eh(0), ep0 = eh(1);
-        const T epc0 = 1 < nrem ? ep0 : T(0);
-        T em = ep0, h = T(1), ap = T(0), bp = T(1);
+                for (int k = 0; k < L; ++k)
+                    if ((flow >> k) & 1u) al[k] = nl_flow(al[k], nlq, nlomq);
+            }
+            // row 0 (F) coefficients, then the forward elimination over rows 1 .. L-2 with x_0 = F
+            const T em0 = eh(0), ep0 = eh(1);
+            const T epc0 = (FULL || 1 < nrem) ? ep0 : T(0);
+            T em = ep0, h = T(1), ap = T(0), bp = T(1);
 #pragma unroll
-        for (int k = 1; k <= L - 2; ++k) {
-            const T ep = eh(k + 1);
-            const T epc = k + 1 < nrem ? ep : T(0);  // row n-2 and the padding rows: no upward coupling
-            const T m = fast_rcp(fmaf(em, h, T(1) + ep));
-            const T g = epc * m;
-            h = T(1) - g;
-            ap = fmaf(em, ap, al[k]) * m;
-            bp = em * bp * m;
-            al[k] = ap;
-            be[k] = bp;
-            ga[k] = g;
-            em = ep;
-        }
-        // back substitution of the x_k = al + be F + ga E representation
+            for (int k = 1; k <= L - 2; ++k) {
+                const T ep = eh(k + 1);
+                const T epc = (FULL || k + 1 < nrem) ? ep : T(0);  // row n-2, padding rows: no upward coupling
+                const T m = fast_rcp(fmaf(em, h, T(1) + ep));
+                const T g = epc * m;
+                h = T(1) - g;
+                ap = fmaf(em, ap, al[k]) * m;
+                bp = em * bp * m;
+                al[k] = ap;
+                be[k] = bp;
+                ga[k] = g;
+                em = ep;
+            }
+            // back substitution of the x_k = al + be F + ga E representation
 #pragma unroll
-        for (int k = L - 3; k >= 1; --k) {
-            const T g = ga[k];
-            al[k] = fmaf(g, al[k + 1], al[k]);
-            be[k] = fmaf(g, be[k + 1], be[k]);
-            ga[k] = g * ga[k + 1];
-        }
-        const T emL = em, epL = eh(L);
-        const T epcL = L < nrem ? epL : T(0);
-        T fa = -em0;
-        const T fb = T(1) + em0 + ep0 - epc0 * be[1];
-        const T fc = -epc0 * ga[1];
-        T fd = fmaf(epc0, al[1], al[0]);
-        const T ea = -emL * be[L - 2];
-        const T eb = T(1) + emL + epL - emL * ga[L - 2];
-        const T ec = -epcL;
-        const T ed = fmaf(emL, al[L - 2], al[L - 1]);
+            for (int k = L - 3; k >= 1; --k) {
+                const T g = ga[k];
+                al[k] = fmaf(g, al[k + 1], al[k]);
+                be[k] = fmaf(g, be[k + 1], be[k]);
+                ga[k] = g * ga[k + 1];
+            }
+            const T emL = em, epL = eh(L);
+            const T epcL = L < nrem ? epL : T(0);
+            fa = -em0;
+            fb = T(1) + em0 + ep0 - epc0 * be[1];
+            fc = -epc0 * ga[1];
+            fd = fmaf(epc0, al[1], al[0]);
+            ea = -emL * be[L - 2];
+            eb = T(1) + emL + epL - emL * ga[L - 2];
+            ec = -epcL;
+            ed = fmaf(emL, al[L - 2], al[L - 1]);
+        };
+        const bool warp_full = __all_sync(0xffffffffu, nrem >= L);
+        if (warp_full) local(std::true_type{});
+        else local(std::false_type{});
         if (seg == 0) {  // row 1 couples to the face value u_0
             fd -= fa * D[at(0)];
             fa = T(0);
@@ -264,9 +298,14 @@ __global__ void __launch_bounds__(TX *SEG, (768 / (TX * SEG)) > 0 ? 768 / (TX * 
             for (int k = 0; k < L; ++k)
                 if ((post >> k) & 1u) al[k] = nl_flow(al[k], nlq, nlomq);
         }
+        if (warp_full) {
 #pragma unroll
-        for (int k = 0; k < L; ++k)
-            if (k < nrem) D[at(g0 + k)] = al[k];
+            for (int k = 0; k < L; ++k) D[at(g0 + k)] = al[k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < L; ++k)
+                if (k < nrem) D[at(g0 + k)] = al[k];
+        }
         fence_proxy_async_smem();
         __syncthreads();
         if (tid == 0) {

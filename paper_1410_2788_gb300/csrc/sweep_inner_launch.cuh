@@ -9,10 +9,10 @@
 
 namespace npb {
 
-// (SEG, L) pairs for x (8 lines per tile: SEG a multiple of 4 fills whole warps) and for y/z
-// (16 lines per tile: SEG even).  L is odd, which keeps the shared-memory rows conflict-free.
-#define NPB_INNER_SEGS_X(X) X(8, 17) X(12, 11) X(16, 9) X(16, 17) X(20, 13) X(24, 11) X(32, 9)
-#define NPB_INNER_SEGS_YZ(X) X(8, 17) X(10, 13) X(16, 9) X(16, 17) X(20, 13) X(24, 11) X(32, 9)
+// (SEG, L) pairs for tiles of 8 lines (SEG a multiple of 4 fills whole warps) and of 16 lines
+// (SEG even).  L is odd, which keeps the shared-memory rows conflict-free.
+#define NPB_INNER_SEGS_X(X) X(4, 17) X(8, 9) X(8, 17) X(12, 11) X(12, 17) X(16, 9) X(16, 17) X(20, 13) X(24, 11) X(24, 17) X(32, 9)
+#define NPB_INNER_SEGS_YZ(X) X(4, 17) X(8, 9) X(8, 17) X(10, 13) X(12, 17) X(16, 9) X(16, 17) X(20, 13) X(24, 11) X(24, 17) X(32, 9)
 
 template <int DIR, int TX, int SEG, int L>
 static cudaError_t launch_inner_shape(const TmaLaunch &P, const TmaGeom &g, int flags, int sm_count, cudaStream_t st) {
@@ -46,7 +46,7 @@ static cudaError_t launch_inner_dir(TmaLaunch &P, const TmaGeom &g, int flags, S
                                  cudaStream_t st) {
 #define NPB_INNER_CASE(SEG_, L_) \
     if (s.seg == SEG_ && s.len == L_) return launch_inner_shape<DIR, TX, SEG_, L_>(P, g, flags, sm_count, st);
-    if constexpr (DIR == DIR_X) { NPB_INNER_SEGS_X(NPB_INNER_CASE) } else { NPB_INNER_SEGS_YZ(NPB_INNER_CASE) }
+    if constexpr (TX == 8) { NPB_INNER_SEGS_X(NPB_INNER_CASE) } else { NPB_INNER_SEGS_YZ(NPB_INNER_CASE) }
 #undef NPB_INNER_CASE
     return cudaErrorInvalidValue;
 }
@@ -61,7 +61,7 @@ static cudaError_t prepare_inner_dir() {
     if (e == cudaSuccess)                                                                                      \
         e = cudaFuncSetAttribute(sweep_inner_kernel<DIR, TX, SEG_, L_>,                                           \
                                  cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-    if constexpr (DIR == DIR_X) { NPB_INNER_SEGS_X(NPB_INNER_PREP) } else { NPB_INNER_SEGS_YZ(NPB_INNER_PREP) }
+    if constexpr (TX == 8) { NPB_INNER_SEGS_X(NPB_INNER_PREP) } else { NPB_INNER_SEGS_YZ(NPB_INNER_PREP) }
 #undef NPB_INNER_PREP
     return e;
 }

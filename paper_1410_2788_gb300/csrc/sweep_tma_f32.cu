@@ -70,7 +70,7 @@ TmaGeom tma_geometry(int dir, int nx, int ny, int nz, int pitch) {
         const int n = dir == DIR_Y ? ny : nz;
         g.nload = (n + 255) / 256;
         g.rows = (n + g.nload - 1) / g.nload;
-        if (g.nload > 1) g.rows = (g.rows + 1) & ~1;  // even: boxes of 16 lines stay 128-byte multiples
+        if (g.nload > 1) g.rows = (g.rows + 3) & ~3;  // boxes of 8 or more lines stay 128-byte multiples
         g.ok = g.nload <= 2 && g.rows <= 256;
     }
     return g;
@@ -153,18 +153,19 @@ cudaError_t prepare_sweep_inner_x();
 cudaError_t prepare_sweep_inner_y();
 cudaError_t prepare_sweep_inner_z();
 
-static const int kInnerSegsX[][2] = {{8, 17}, {12, 11}, {16, 9}, {16, 17}, {20, 13}, {24, 11}, {32, 9}};
-static const int kInnerSegsYZ[][2] = {{8, 17}, {10, 13}, {16, 9}, {16, 17}, {20, 13}, {24, 11}, {32, 9}};
+static const int kInnerSegsX[][2] = {{4, 17}, {8, 9},   {8, 17},  {12, 11}, {12, 17}, {16, 9},
+                                     {16, 17}, {20, 13}, {24, 11}, {24, 17}, {32, 9}};
+static const int kInnerSegsYZ[][2] = {{4, 17}, {8, 9},   {8, 17},  {10, 13}, {12, 17}, {16, 9},
+                                      {16, 17}, {20, 13}, {24, 11}, {24, 17}, {32, 9}};
 
 int inner_shapes(int dir, SweepShape *out, int max) {
     int n = 0;
-    if (dir == DIR_X) {
-        for (const auto &p : kInnerSegsX)
-            if (n < max) out[n++] = SweepShape{8, p[0], p[1], 2};
-    } else {
+    if (dir != DIR_X) {
         for (const auto &p : kInnerSegsYZ)
             if (n < max) out[n++] = SweepShape{16, p[0], p[1], 2};
     }
+    for (const auto &p : kInnerSegsX)  // 8 lines per tile: x, and y/z in 32-byte boxes
+        if (n < max) out[n++] = SweepShape{8, p[0], p[1], 2};
     return n;
 }
 

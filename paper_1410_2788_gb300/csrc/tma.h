@@ -23,15 +23,17 @@ cudaError_t launch_sweep_tma(int dir, TmaLaunch &P, const TmaGeom &g, int flags,
                              cudaStream_t st);
 cudaError_t prepare_sweep_tma();
 
-// Lines per tile of the tensor-map variants: x sweeps 8; y/z sweeps 32 or 16.
-inline int tma_variant_tx(int dir, int v) { return dir == DIR_X ? 8 : (v == 0 ? 32 : 16); }
+// Lines per tile of the tensor-map variants: x sweeps 8 (variant 0 only); y/z sweeps 32, 16 or 8.
+constexpr int kTmaVariants = 3;
+inline int tma_variant_count(int dir) { return dir == DIR_X ? 1 : kTmaVariants; }
+inline int tma_variant_tx(int dir, int v) { return dir == DIR_X ? 8 : (v == 0 ? 32 : (v == 1 ? 16 : 8)); }
 inline int tma_variant(int dir, int tx) {
     if (dir == DIR_X) return tx == 8 ? 0 : -1;
-    return tx == 32 ? 0 : (tx == 16 ? 1 : -1);
+    return tx == 32 ? 0 : (tx == 16 ? 1 : (tx == 8 ? 2 : -1));
 }
 int tma_shapes(int dir, SweepShape *out, int max);
 
-// Interior-row sweeps (kind 2): x tiles of 8 lines, y/z tiles of 16.
+// Interior-row sweeps (kind 2): x tiles of 8 lines, y/z tiles of 16 or 8.
 cudaError_t launch_sweep_inner(int dir, TmaLaunch &P, const TmaGeom &g, int flags, SweepShape s, int sm_count,
                             cudaStream_t st);
 cudaError_t prepare_sweep_inner();

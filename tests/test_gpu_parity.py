@@ -91,7 +91,7 @@ def test_stage_parity(npb, ctx, O, precision, tol, leg, scheme):
     _stage_check(npb, ctx, O, precision, tol, leg, scheme)
 
 
-@pytest.mark.parametrize("shape", range(7))
+@pytest.mark.parametrize("shape", range(22))
 @pytest.mark.parametrize("leg,scheme", [(0, 2), (2, 2), (1, 1), (3, 1)])
 def test_inner_sweep_stage_parity(npb, O, shape, leg, scheme):
     """The interior-row FP32 sweeps (kind 2) pinned for all three directions on the ragged
@@ -102,7 +102,8 @@ def test_inner_sweep_stage_parity(npb, O, shape, leg, scheme):
         p = small_molecule()
         dims = npb.grid_shape(p)[::-1]
         for d in range(3):
-            tx, seg, ln = INNER_SHAPES[min(d, 1)][min(shape, len(INNER_SHAPES[min(d, 1)]) - 1)]
+            lst = INNER_SHAPES[min(d, 1)]
+            tx, seg, ln = lst[shape % len(lst)]
             npb.npb_tune_set(c, 1, d, dims[d], npb.KIND_TMA_INNER, tx, seg, ln)
         _stage_check(npb, c, O, 1, 1e-4, leg, scheme)
     finally:
@@ -320,8 +321,12 @@ def test_graph_replay_is_bitwise_stable(npb, ctx):
 TMA_SHAPES = {0: [(8, 2, 17), (8, 4, 9), (8, 4, 17), (8, 8, 13), (8, 8, 17), (8, 16, 11), (8, 16, 17), (8, 32, 9)],
               1: [(32, 2, 17), (32, 4, 9), (32, 4, 17), (32, 8, 13), (32, 8, 17), (32, 16, 11), (32, 16, 17),
                   (16, 4, 17), (16, 8, 13), (16, 8, 17), (16, 16, 11), (16, 16, 17), (16, 32, 9)]}
-INNER_SHAPES = {0: [(8, s, l) for s, l in [(8, 17), (12, 11), (16, 9), (16, 17), (20, 13), (24, 11), (32, 9)]],
-                1: [(16, s, l) for s, l in [(8, 17), (10, 13), (16, 9), (16, 17), (20, 13), (24, 11), (32, 9)]]}
+_INNER_SEGS_8 = [(4, 17), (8, 9), (8, 17), (12, 11), (12, 17), (16, 9), (16, 17), (20, 13), (24, 11), (24, 17),
+                 (32, 9)]
+_INNER_SEGS_16 = [(4, 17), (8, 9), (8, 17), (10, 13), (12, 17), (16, 9), (16, 17), (20, 13), (24, 11), (24, 17),
+                  (32, 9)]
+INNER_SHAPES = {0: [(8, s, l) for s, l in _INNER_SEGS_8],
+                1: [(16, s, l) for s, l in _INNER_SEGS_16] + [(8, s, l) for s, l in _INNER_SEGS_8]}
 CLASSIC_SHAPES = [(16, 2, 17), (16, 4, 9), (16, 4, 17), (16, 8, 9), (16, 8, 13), (16, 8, 17), (16, 16, 9),
                   (16, 16, 11), (16, 16, 17), (16, 32, 9), (32, 8, 17), (32, 16, 9)]
 
