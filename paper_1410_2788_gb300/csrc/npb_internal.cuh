@@ -52,7 +52,7 @@ struct LegDev {
     int32_t nl_on;             // 1: solvent nodes get the nonlinear stage
     int32_t eps_mode;          // 0 harmonic, 1 midpoint
     float rEf[3], nl_qf, nl_omqf, srcf;  // the same constants rounded once to FP32 (FP32 sweeps)
-    const int2 *ent_xq;                  // charge entries as (x, FP32 qtilde), same order as ent_x
+    const int2 *ent_xq;                  // charge entries as (x | y << 16, FP32 qtilde), ent_x's order
 };
 
 // Stage flags for the sweep kernels.

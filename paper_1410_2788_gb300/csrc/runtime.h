@@ -96,7 +96,7 @@ struct npb_grid {
     uint32_t *d_half[3] = {nullptr, nullptr, nullptr};
     int32_t *d_line_begin = nullptr, *d_line_count = nullptr, *d_ent_x = nullptr;
     double *d_ent_qt = nullptr;
-    int2 *d_ent_xq = nullptr;  // (x, FP32 qtilde) of each entry, for the FP32 sweeps' fused source
+    int2 *d_ent_xq = nullptr;  // (x | y << 16, FP32 qtilde) of each entry: the FP32 sweeps' fused source
     int64_t *d_ent_off = nullptr;
     int n_ent = 0;
     double *d_bc[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [medium][0 fp64 | 1 fp32 pairs]

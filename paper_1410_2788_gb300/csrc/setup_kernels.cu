@@ -184,7 +184,7 @@ __global__ void k_charge_compact(GridGeom g, const RawEntry *__restrict__ bucket
         ent_x[b + i] = r.x;
         ent_qt[b + i] = r.val;
         ent_off[b + i] = ((int64_t)z * g.ny + y) * g.pitch + r.x;
-        if (ent_xq) ent_xq[b + i] = make_int2(r.x, __float_as_int((float)r.val));
+        if (ent_xq) ent_xq[b + i] = make_int2(r.x | (y << 16), __float_as_int((float)r.val));
     }
 }
 

@@ -24,6 +24,10 @@
 
 namespace npb {
 
+// Charge entries of the next x tile held in registers per thread (the fused source stage); a
+// tile with more than kSrcRegs * threads entries reads the rest when they are applied.
+constexpr int kSrcRegs = 2;
+
 // Largest PCR stride for SEG segments (the highest power of two below SEG).
 template <int SEG>
 __host__ __device__ constexpr int pcr_top() {
@@ -153,22 +157,42 @@ __global__ void __launch_bounds__(TX *SEG, (768 / (TX * SEG)) > 0 ? 768 / (TX * 
         if (t < total) issue(t, 0);
     }
     __syncthreads();  // barriers initialised, the first tile's indices visible
+
+    // Fused source stage (x sweep).  The charge entries of an x tile are contiguous in the charge
+    // list (lines ordered by z, then y), each a node (x | y << 16, FP32 qtilde).  They are read one
+    // tile ahead, one or two per thread, and added to the tile's staged rows right after its copy
+    // has landed, followed by one block barrier (tiles without charges skip both); the first tile
+    // of a block is handled before the loop.
+    constexpr int NT = TX * SEG;
+    const bool fuse_src = DIR == DIR_X && (flags & FUSE_PRE_SRC) != 0;
+    auto src_range = [&](int q, int &tb, int &te) {  // entry range of stage q's tile
+        const int4 ti = tinfo[q];
+        const LegDev &lg = P.legs[ti.x];
+        const int y0 = 1 + ti.y * TX, y1 = min(y0 + TX, lg.ny - 1);  // lines y0 .. y1-1
+        const int ln = (1 + ti.z) * lg.ny;
+        tb = lg.line_begin[ln + y0];
+        te = lg.line_begin[ln + y1 - 1] + lg.line_count[ln + y1 - 1];
+    };
+    auto src_apply = [&](int q, int2 v) {  // one entry into stage q's rows
+        const int4 ti = tinfo[q];
+        const int l = (v.x >> 16) - (1 + ti.y * TX), x = v.x & 0xffff;
+        data(q)[l * P.sx + x] += P.legs[ti.x].srcf * __int_as_float(v.y);
+    };
+    if (fuse_src && t < total) {
+        int tb, te;
+        src_range(0, tb, te);
+        const int2 *ent = P.legs[tinfo[0].x].ent_xq;
+        const bool ok = mbar_wait_bounded(&bar[0], 0);
+        if (ok)
+            for (int e = tb + tid; e < te; e += NT) src_apply(0, ent[e]);
+        else if (tid == 0)
+            atomicExch(P.err, 1);
+    }
+    int2 sv[kSrcRegs];
+    int cur_tb = 0, cur_te = 0;  // entries held in sv for the tile solved next (none for the first)
     for (; t < total; t += gridDim.x, ++it) {
         const int s = it & 1;
         const int tn = t + gridDim.x;
-        // the tile's indices were written before the last block barrier: start the charge-list
-        // reads of the fused source stage now, under the wait for the tile's data
-        int e0 = 0, ne = 0;
-        if (DIR == DIR_X && (flags & FUSE_PRE_SRC)) {
-            const int4 ti = tinfo[s];
-            const LegDev &lg = P.legs[ti.x];
-            const int yl = 1 + ti.y * TX + line;
-            if (yl <= lg.ny - 2) {
-                const int ln = (1 + ti.z) * lg.ny + yl;
-                e0 = lg.line_begin[ln];
-                ne = lg.line_count[ln];
-            }
-        }
         if (tid == 0 && tn < total) {
             bulk_wait_read_all();
             issue(tn, s ^ 1);
@@ -181,6 +205,14 @@ __global__ void __launch_bounds__(TX *SEG, (768 / (TX * SEG)) > 0 ? 768 / (TX * 
                 bulk_wait_all();
             }
             return;
+        }
+        if (cur_te > cur_tb) {  // block-uniform: tau Q into this tile's rows, then a barrier
+#pragma unroll
+            for (int r = 0; r < kSrcRegs; ++r)
+                if (cur_tb + tid + r * NT < cur_te) src_apply(s, sv[r]);
+            const int2 *ent = P.legs[tinfo[s].x].ent_xq;
+            for (int e = cur_tb + tid + kSrcRegs * NT; e < cur_te; e += NT) src_apply(s, ent[e]);
+            __syncthreads();
         }
 
         const int4 ti = tinfo[s];
@@ -210,13 +242,10 @@ __global__ void __launch_bounds__(TX *SEG, (768 / (TX * SEG)) > 0 ? 768 / (TX * 
 
         // LODIE2 stage S fused into the x sweep: tau Q at this thread's own charge nodes (each
         // thread scans its line's charge list, so no other thread's rows are touched)
-        if (DIR == DIR_X && (flags & FUSE_PRE_SRC)) {
-            for (int e = e0; e < e0 + ne; ++e) {
-                const int2 v = lg.ent_xq[e];
-                const int k = v.x - g0;
-                if (k >= 0 && k < L && k < nrem) D[at(v.x)] += lg.srcf * __int_as_float(v.y);
-            }
-        }
+        // the next tile's charge entries: range now, entries after the local elimination
+        const bool src_next = fuse_src && tn < total;
+        int ntb = 0, nte = 0;
+        if (src_next) src_range(s ^ 1, ntb, nte);
         // row n-2 of the line: move its face coupling eps u_{n-1} to the right-hand side (after
         // the inflowing nonlinear stage, so the flow sees the bare node value)
         if (nrem >= 1 && nrem <= L) {
@@ -285,6 +314,14 @@ __global__ void __launch_bounds__(TX *SEG, (768 / (TX * SEG)) > 0 ? 768 / (TX * 
             fd -= fa * D[at(0)];
             fa = T(0);
         }
+        if (src_next) {
+            const int2 *ent = P.legs[tinfo[s ^ 1].x].ent_xq;
+#pragma unroll
+            for (int r = 0; r < kSrcRegs; ++r) {
+                const int e = ntb + tid + r * NT;
+                sv[r] = e < nte ? ent[e] : make_int2(0, 0);
+            }
+        }
         T F_, E_;
         inner_ends<TX, SEG>(fa, fb, fc, fd, ea, eb, ec, ed, seg, line, fbuf, pbuf, ebuf, F_, E_);
 
@@ -306,6 +343,8 @@ __global__ void __launch_bounds__(TX *SEG, (768 / (TX * SEG)) > 0 ? 768 / (TX * 
             for (int k = 0; k < L; ++k)
                 if (k < nrem) D[at(g0 + k)] = al[k];
         }
+        cur_tb = ntb;
+        cur_te = nte;
         fence_proxy_async_smem();
         __syncthreads();
         if (tid == 0) {
