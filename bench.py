@@ -258,7 +258,7 @@ def serving_run(npb, seconds: float, rate: float = 50.0, fifo_requests: int = 12
 
 def _kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("sweep_kernel.cuh", "sweep_launch.cuh"):
+    for f in ("sweep_kernel.cuh", "sweep_tma.cuh", "sweep_inner.cuh", "sweep_inner_launch.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1410_2788_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
