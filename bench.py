@@ -194,6 +194,57 @@ def cpu_baseline(problem, w, budget_s: float = 12.0):
             "sample": f"{reps} RE+V solve(s) of the same molecule with {n_s} steps per dt leg"}
 
 
+def batch_run(npb, count: int, reps: int = 3):
+    """The batched workload: `count` seeded random-walk molecules of 200-5,000 atoms (log-uniform),
+    grids 65^3-161^3 by the grid-size rule, RE+V with FP32 sweeps and FP64 energies.  Times
+    npb_energy_batch (equal-size grids share persistent launches; one CUDA graph per batch) against
+    the same grids solved one npb_energy call at a time, both after a warm-up call, with L2 flushed
+    before every timed call (CUDA events on the context's stream)."""
+    import torch
+
+    import npb_inputs as I
+
+    mols = I.batch_molecules(count)
+    ctx = npb.npb_ctx_create(0, 0)
+    stream = torch.cuda.Stream()
+    npb.npb_ctx_set_stream(ctx, stream.cuda_stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    try:
+        grids = [npb.npb_grid_create(ctx, p) for p in mols]
+        o32 = npb.make_opts(DT, ALPHA, NSTEPS, precision=npb.NPB_FP32_SWEEP)
+        pts = sum((p.n[0] - 2) * (p.n[1] - 2) * (p.n[2] - 2) for p in mols) * 6 * NSTEPS
+
+        def timed(fn):
+            ms = []
+            with torch.cuda.stream(stream):
+                fn()
+                for _ in range(reps):
+                    flush.zero_()
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    fn()
+                    b.record(stream)
+                    torch.cuda.synchronize()
+                    ms.append(a.elapsed_time(b))
+            return sorted(ms)[len(ms) // 2]
+
+        out_b = []
+        t_batch = timed(lambda: out_b.append(npb.npb_energy_batch(grids, o32)))
+        out_s = []
+        t_seq = timed(lambda: out_s.append([npb.npb_energy(g, o32) for g in grids]))
+        for g in grids:
+            npb.npb_grid_destroy(g)
+    finally:
+        npb.npb_ctx_destroy(ctx)
+    sizes = sorted({p.n[0] for p in mols})
+    return {"molecules": count, "grids": sizes, "atoms": [min(p.n_atoms for p in mols), max(p.n_atoms for p in mols)],
+            "point_steps": pts, "ms_batch": t_batch, "Mpoint_steps_per_s": pts / t_batch / 1e3,
+            "solves_per_s": count / t_batch * 1e3, "ms_one_at_a_time": t_seq,
+            "one_at_a_time_Mpoint_steps_per_s": pts / t_seq / 1e3,
+            "same_results": bool(out_b[-1] == out_s[-1]),
+            "note": "median of %d calls; equal-size grids share one launch per direction per step" % reps}
+
+
 def serving_run(npb, seconds: float, rate: float = 50.0, fifo_requests: int = 12):
     """Poisson arrivals (seeded stream of random-walk molecules, 100-20,000 atoms, h 0.25/0.5 A)
     through npb_submit/npb_poll with continuous batching, FP32 sweeps; then the first
@@ -433,6 +484,7 @@ def run_ours(args):
         return 0
     base = cpu_baseline(problem, w) if world == 1 else None
     serving = serving_run(npb, args.serving_seconds) if (world == 1 and args.serving_seconds > 0) else None
+    batch = batch_run(npb, args.batch_count) if (world == 1 and args.batch_count > 0) else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
@@ -455,6 +507,7 @@ def run_ours(args):
                 "call": "npb_grid_create + npb_energy + npb_grid_destroy from pinned host arrays"},
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "serving": serving,
+        "batch": batch,
         "clocks": clk,
         "autotune": tuning[:0] if not args.verbose else tuning,
     }
@@ -474,6 +527,8 @@ def main(argv=None):
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--verbose", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=64,
+                    help="molecules in the batched-workload measurement (0 skips it)")
     ap.add_argument("--serving-seconds", type=float, default=5.0,
                     help="length of the Poisson serving stream measured after the main line (0: skip)")
     args = ap.parse_args(argv)

@@ -169,6 +169,16 @@ int npb_lod_solve(npb_grid *grid, const npb_opts *opts, int32_t medium, double d
  * of Eqs. (rich) and (deltaG3).  Blocks until the value is on the host. */
 int npb_energy(npb_grid *grid, const npb_opts *opts, double *dG_kcal_mol);
 
+/* npb_energy for n_grids molecules at once (the batched workload of many uneven grids): every
+ * grid runs the same opts; grids of equal size share one persistent sweep launch per direction
+ * at each LOD step (Sec. 3.1) over all their legs, and the whole batch -- leg starts, steps and
+ * the FP64 energies of Eqs. (rich) and (deltaG3) -- runs as one CUDA graph, kept for repeat
+ * calls with the same grids, opts and solver shapes.  dG_kcal_mol[i] receives grid i's energy;
+ * each equals npb_energy(grids[i], opts) bit for bit.  The grids must belong to one context and
+ * appear once each; the call blocks until every value is on the host.  NPB_ETIMEOUT when a
+ * bounded device wait expired (all values are then unreliable). */
+int npb_energy_batch(npb_grid *const *grids, int32_t n_grids, const npb_opts *opts, double *dG_kcal_mol);
+
 /* Copy leg `leg` (NPB_LEG_*) of the last solve to host_out as dense FP64 values of u
  * (dimensionless), nz*ny*nx of them, x fastest.  n_elems must equal nx*ny*nz. */
 int npb_potential(npb_grid *grid, int32_t leg, double *host_out, size_t n_elems);

@@ -240,7 +240,7 @@ def large_20k() -> Problem:
 
 def batch_molecules(count: int = 64, lo_atoms: int = 200, hi_atoms: int = 5000,
                     n_min: int = 65, n_max: int = 161, h: float = 0.5) -> list[Problem]:
-    """Seeded batch: atom counts log-uniform on [lo, hi]; grid by the 40 A^3/atom rule."""
+    """Seeded batch: atom counts log-uniform on [lo, hi]; each grid by grid_size_for."""
     base = SEED_BASE + 3
     sizes = Xoshiro256ss(base + 10**6)
     out = []

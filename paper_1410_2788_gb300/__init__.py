@@ -80,6 +80,7 @@ SIGNATURES = {
     "npb_grid_footprint": (_SZ, [ctypes.POINTER(npb_problem), _I32]),
     "npb_lod_solve": (_I, [_V, ctypes.POINTER(npb_opts), _I32, ctypes.c_double]),
     "npb_energy": (_I, [_V, ctypes.POINTER(npb_opts), _dp]),
+    "npb_energy_batch": (_I, [ctypes.POINTER(_V), _I32, ctypes.POINTER(npb_opts), ctypes.POINTER(ctypes.c_double)]),
     "npb_potential": (_I, [_V, _I32, _dp, _SZ]),
     "npb_apply": (_I, [_V, ctypes.POINTER(npb_opts), _I32, _I32, _dp, _SZ]),
     "npb_grid_export": (_I, [_V, _I32, _V, _SZ]),
@@ -214,6 +215,15 @@ def npb_energy(grid: int, opts: npb_opts) -> float:
     out = ctypes.c_double()
     _check(load_library().npb_energy(grid, ctypes.byref(opts), ctypes.byref(out)))
     return out.value
+
+
+def npb_energy_batch(grids, opts: npb_opts) -> list:
+    """RE+V energies (kcal/mol) of several grids in one batched, graph-captured solve."""
+    n = len(grids)
+    arr = (_V * n)(*grids)
+    out = (ctypes.c_double * n)()
+    _check(load_library().npb_energy_batch(arr, n, ctypes.byref(opts), out))
+    return list(out)
 
 
 def npb_potential(grid: int, leg: int, shape) -> np.ndarray:

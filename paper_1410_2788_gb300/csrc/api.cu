@@ -36,14 +36,6 @@ int npb::fail(int code, const char *fmt, ...) {
     return code;
 }
 
-#define CU(call)                                                                          \
-    do {                                                                                  \
-        cudaError_t e_ = (call);                                                          \
-        if (e_ != cudaSuccess)                                                            \
-            return fail(NPB_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
-                        __FILE__, __LINE__);                                              \
-    } while (0)
-
 extern "C" const char *npb_last_error(void) { return t_err.c_str(); }
 extern "C" const char *npb_version(void) { return "npb-lod-gb300 1.0 (sm_103a)"; }
 
@@ -192,6 +184,7 @@ extern "C" void npb_ctx_destroy(npb_ctx *ctx) {
     serve_shutdown(ctx);
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    batch_forget(ctx, nullptr);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     delete ctx;
 }
@@ -311,6 +304,7 @@ void npb::grid_free(npb_grid *g) {
     if (!g) return;
     cudaSetDevice(g->ctx->device);
     cudaStreamSynchronize(g->ctx->stream);
+    batch_forget(g->ctx, g);
     for (auto &c : g->graphs) {
         if (c.exec) cudaGraphExecDestroy(c.exec);
     }

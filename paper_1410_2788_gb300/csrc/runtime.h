@@ -29,6 +29,16 @@ extern const char *kKernelNames[K_COUNT];
 
 int fail(int code, const char *fmt, ...);
 
+// Return NPB_ECUDA with the failing call's text when a CUDA call fails.
+#define CU(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(NPB_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                              \
+    } while (0)
+
+
 // Per-kernel CUDA-event timing (only while enabled; graphs are bypassed then).
 struct Profiler {
     struct Pending {
@@ -47,6 +57,7 @@ struct Profiler {
 };
 
 struct ServeState;  // serving scheduler (serve.cu)
+struct BatchPlan;   // npb_energy_batch plan (batch.cu)
 
 inline int64_t tune_key(int prec, int dir, int n) { return ((int64_t)prec << 40) | ((int64_t)dir << 32) | n; }
 
@@ -64,6 +75,8 @@ struct npb_ctx {
     std::mutex tune_mu;
     std::map<int64_t, npb::SweepShape> tuned;  // autotuned line-solver shapes
     npb::ServeState *serve = nullptr;
+    std::mutex batch_mu;
+    std::vector<npb::BatchPlan *> batches;  // npb_energy_batch plans: leg tables and graphs
     int alloc(void **p, size_t bytes);
     void release(void *p, size_t bytes);
 };
@@ -148,6 +161,7 @@ int grid_check_err(Grid *g, cudaStream_t st, int host_copy);
 int init_legs(Grid *g, int prec, const int *legs, int n, cudaStream_t st);
 int enqueue_energy(Grid *g, const npb_opts *o, cudaStream_t st);
 void serve_shutdown(Ctx *ctx);
+void batch_forget(Ctx *ctx, Grid *g);  // drop batch plans naming g (all plans when g is null)
 
 }  // namespace npb
 

@@ -121,6 +121,10 @@ __global__ void __launch_bounds__(TX *SEG, (768 / (TX * SEG)) > 0 ? 768 / (TX * 
     off += tma_align((size_t)(TX * SEG + 2 * kRows) * 16 + (size_t)TX * SEG * 4);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + off);
     int4 *tinfo = reinterpret_cast<int4 *>(bar + 2);  // (leg, a, b) of the tile in each stage
+    // a leg's tensor maps and constants: inline in the launch, or in the device-memory leg table
+    auto umap = [&](int leg) -> const CUtensorMap * { return P.table ? &P.table[leg].umap : &P.umap[leg]; };
+    auto mmap = [&](int leg) -> const CUtensorMap * { return P.table ? &P.table[leg].mmap : &P.mmap[leg]; };
+    auto legp = [&](int leg) -> const LegDev & { return P.table ? P.table[leg].dev : P.legs[leg]; };
     for (int i = tid; i < 2 * kRows; i += TX * SEG) {  // identity rows; the margins are never written again
         fbuf[TX * SEG + i] = make_float4(0.f, 1.f, 0.f, 0.f);
     }
@@ -132,20 +136,20 @@ __global__ void __launch_bounds__(TX *SEG, (768 / (TX * SEG)) > 0 ? 768 / (TX * 
     auto issue = [&](int t, int s) {  // thread 0 only; the other threads read the tile's indices
         const int leg = t / tpl, r = t - leg * tpl, b = r / P.tiles_a, a = r - b * P.tiles_a;
         tinfo[s] = make_int4(leg, a, b, 0);
-        const bool has_mask = P.legs[leg].mask != nullptr;
+        const bool has_mask = legp(leg).mask != nullptr;
         mbar_expect_tx(&bar[s], P.tx_u + (has_mask ? P.tx_m : 0u));
         if (DIR == DIR_X) {
             const int y0 = 1 + a * TX, z = 1 + b;
-            tma_load_4d(data(s), &P.umap[leg], &bar[s], 0, 0, y0, z);
-            if (has_mask) tma_load_3d(msk(s), &P.mmap[leg], &bar[s], 0, y0, z);
+            tma_load_4d(data(s), umap(leg), &bar[s], 0, 0, y0, z);
+            if (has_mask) tma_load_3d(msk(s), mmap(leg), &bar[s], 0, y0, z);
         } else {
             const int x0 = a * TX, c = 1 + b;
             for (int q = 0; q < P.nload; ++q) {
                 T *dst = data(s) + (size_t)q * (dbox / 4);
-                if (DIR == DIR_Y) tma_load_3d(dst, &P.umap[leg], &bar[s], x0, q * P.rows, c);
-                else tma_load_3d(dst, &P.umap[leg], &bar[s], x0, c, q * P.rows);
+                if (DIR == DIR_Y) tma_load_3d(dst, umap(leg), &bar[s], x0, q * P.rows, c);
+                else tma_load_3d(dst, umap(leg), &bar[s], x0, c, q * P.rows);
             }
-            if (has_mask) tma_load_3d(msk(s), &P.mmap[leg], &bar[s], 0, x0, c);
+            if (has_mask) tma_load_3d(msk(s), mmap(leg), &bar[s], 0, x0, c);
         }
     };
 
@@ -167,7 +171,7 @@ __global__ void __launch_bounds__(TX *SEG, (768 / (TX * SEG)) > 0 ? 768 / (TX * 
     const bool fuse_src = DIR == DIR_X && (flags & FUSE_PRE_SRC) != 0;
     auto src_range = [&](int q, int &tb, int &te) {  // entry range of stage q's tile
         const int4 ti = tinfo[q];
-        const LegDev &lg = P.legs[ti.x];
+        const LegDev &lg = legp(ti.x);
         const int y0 = 1 + ti.y * TX, y1 = min(y0 + TX, lg.ny - 1);  // lines y0 .. y1-1
         const int ln = (1 + ti.z) * lg.ny;
         tb = lg.line_begin[ln + y0];
@@ -176,12 +180,12 @@ __global__ void __launch_bounds__(TX *SEG, (768 / (TX * SEG)) > 0 ? 768 / (TX * 
     auto src_apply = [&](int q, int2 v) {  // one entry into stage q's rows
         const int4 ti = tinfo[q];
         const int l = (v.x >> 16) - (1 + ti.y * TX), x = v.x & 0xffff;
-        data(q)[l * P.sx + x] += P.legs[ti.x].srcf * __int_as_float(v.y);
+        data(q)[l * P.sx + x] += legp(ti.x).srcf * __int_as_float(v.y);
     };
     if (fuse_src && t < total) {
         int tb, te;
         src_range(0, tb, te);
-        const int2 *ent = P.legs[tinfo[0].x].ent_xq;
+        const int2 *ent = legp(tinfo[0].x).ent_xq;
         const bool ok = mbar_wait_bounded(&bar[0], 0);
         if (ok)
             for (int e = tb + tid; e < te; e += NT) src_apply(0, ent[e]);
@@ -210,14 +214,14 @@ __global__ void __launch_bounds__(TX *SEG, (768 / (TX * SEG)) > 0 ? 768 / (TX * 
 #pragma unroll
             for (int r = 0; r < kSrcRegs; ++r)
                 if (cur_tb + tid + r * NT < cur_te) src_apply(s, sv[r]);
-            const int2 *ent = P.legs[tinfo[s].x].ent_xq;
+            const int2 *ent = legp(tinfo[s].x).ent_xq;
             for (int e = cur_tb + tid + kSrcRegs * NT; e < cur_te; e += NT) src_apply(s, ent[e]);
             __syncthreads();
         }
 
         const int4 ti = tinfo[s];
         const int leg = ti.x, a = ti.y, bb = ti.z;
-        const LegDev &lg = P.legs[leg];
+        const LegDev &lg = legp(leg);
         const int ndir = DIR == DIR_X ? lg.nx : (DIR == DIR_Y ? lg.ny : lg.nz);
         const T rE0 = lg.rEf[0], rE1 = lg.rEf[1], rE2 = lg.rEf[2];
         const T nlq = lg.nl_qf, nlomq = lg.nl_omqf;
@@ -315,7 +319,7 @@ __global__ void __launch_bounds__(TX *SEG, (768 / (TX * SEG)) > 0 ? 768 / (TX * 
             fa = T(0);
         }
         if (src_next) {
-            const int2 *ent = P.legs[tinfo[s ^ 1].x].ent_xq;
+            const int2 *ent = legp(tinfo[s ^ 1].x).ent_xq;
 #pragma unroll
             for (int r = 0; r < kSrcRegs; ++r) {
                 const int e = ntb + tid + r * NT;
@@ -349,13 +353,13 @@ __global__ void __launch_bounds__(TX *SEG, (768 / (TX * SEG)) > 0 ? 768 / (TX * 
         __syncthreads();
         if (tid == 0) {
             if (DIR == DIR_X) {
-                tma_store_4d(&P.umap[leg], D, 0, 0, 1 + a * TX, 1 + bb);
+                tma_store_4d(umap(leg), D, 0, 0, 1 + a * TX, 1 + bb);
             } else {
                 const int x0 = a * TX, c = 1 + bb;
                 for (int q = 0; q < P.nload; ++q) {
                     const T *src = D + (size_t)q * (dbox / 4);
-                    if (DIR == DIR_Y) tma_store_3d(&P.umap[leg], src, x0, q * P.rows, c);
-                    else tma_store_3d(&P.umap[leg], src, x0, c, q * P.rows);
+                    if (DIR == DIR_Y) tma_store_3d(umap(leg), src, x0, q * P.rows, c);
+                    else tma_store_3d(umap(leg), src, x0, c, q * P.rows);
                 }
             }
             bulk_commit();

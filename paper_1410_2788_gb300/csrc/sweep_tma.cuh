@@ -29,10 +29,18 @@ namespace npb {
 
 constexpr int kTmaMaxLegs = 8;
 
+// One leg of a launch whose legs live in device memory (any number of legs of one grid size).
+struct alignas(128) LegTma {
+    CUtensorMap umap;  // the leg's state, box of this launch's direction and tile width
+    CUtensorMap mmap;  // its line-major node mask (unused when dev.mask is null)
+    LegDev dev;
+};
+
 struct TmaLaunch {
     CUtensorMap umap[kTmaMaxLegs];  // state of each leg (box per direction)
     CUtensorMap mmap[kTmaMaxLegs];  // node mask of each leg (unused when legs[i].mask is null)
     LegDev legs[kTmaMaxLegs];
+    const LegTma *table;            // when set: the legs are table[0 .. n_legs), the arrays above unused
     int32_t *err;                   // set to 1 when a bounded wait expires
     int32_t n_legs, tiles_a, tiles_b;
     int32_t rows, nload;            // y/z: rows per box and boxes per tile

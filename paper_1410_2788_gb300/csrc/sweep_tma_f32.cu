@@ -176,8 +176,7 @@ cudaError_t prepare_sweep_inner() {
     return e;
 }
 
-static void tma_tiles(int dir, TmaLaunch &P, const TmaGeom &g, SweepShape s) {
-    const int nx = P.legs[0].nx, ny = P.legs[0].ny, nz = P.legs[0].nz;
+static void tma_tiles(int dir, TmaLaunch &P, const TmaGeom &g, SweepShape s, int nx, int ny, int nz) {
     P.mwpr = g.mwpr;
     P.rows = g.rows;
     P.nload = g.nload;
@@ -197,7 +196,22 @@ static void tma_tiles(int dir, TmaLaunch &P, const TmaGeom &g, SweepShape s) {
 
 cudaError_t launch_sweep_inner(int dir, TmaLaunch &P, const TmaGeom &g, int flags, SweepShape s, int sm_count,
                             cudaStream_t st) {
-    tma_tiles(dir, P, g, s);
+    if (P.table) return cudaErrorInvalidValue;
+    tma_tiles(dir, P, g, s, P.legs[0].nx, P.legs[0].ny, P.legs[0].nz);
+    if (dir == DIR_X) return launch_sweep_inner_x(P, g, flags, s, sm_count, st);
+    if (dir == DIR_Y) return launch_sweep_inner_y(P, g, flags, s, sm_count, st);
+    return launch_sweep_inner_z(P, g, flags, s, sm_count, st);
+}
+
+cudaError_t launch_sweep_inner_table(int dir, const LegTma *table, int n_legs, int nx, int ny, int nz,
+                                    int32_t *err, const TmaGeom &g, int flags, SweepShape s, int sm_count,
+                                    cudaStream_t st) {
+    TmaLaunch P;
+    memset(&P, 0, sizeof P);
+    P.table = table;
+    P.n_legs = n_legs;
+    P.err = err;
+    tma_tiles(dir, P, g, s, nx, ny, nz);
     if (dir == DIR_X) return launch_sweep_inner_x(P, g, flags, s, sm_count, st);
     if (dir == DIR_Y) return launch_sweep_inner_y(P, g, flags, s, sm_count, st);
     return launch_sweep_inner_z(P, g, flags, s, sm_count, st);

@@ -10,12 +10,6 @@
 
 using namespace npb;
 
-#define CU(call)                                                                                   \
-    do {                                                                                           \
-        cudaError_t e_ = (call);                                                                   \
-        if (e_ != cudaSuccess) return fail(NPB_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
-    } while (0)
-
 extern "C" int npb_autotune(npb_grid *g, const npb_opts *o, int32_t reps, char *report, size_t report_len) {
     if (!g || !o) return fail(NPB_EINVAL, "NULL argument");
     if (reps <= 0) reps = 5;

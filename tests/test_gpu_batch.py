@@ -1,0 +1,93 @@
+"""npb_energy_batch: many molecules of uneven grid sizes in shared persistent launches."""
+import numpy as np
+import pytest
+
+import npb_inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def npb():
+    import paper_1410_2788_gb300 as m
+    from paper_1410_2788_gb300 import build
+
+    build.build()
+    return m
+
+
+@pytest.fixture(scope="module")
+def O(oracle_lib):
+    import os
+
+    oracle_lib.set_threads(os.cpu_count() or 8)
+    return oracle_lib
+
+
+def _mols():
+    # grids 65^3 (three molecules), 97^3 (two) and 57^3 (one): three groups of uneven size
+    spec = [(40, 65), (100, 65), (300, 97), (110, 65), (450, 97), (30, 57)]
+    return [I.random_walk_molecule(na, n, 0.5, seed=I.SEED_BASE + 300 + i) for i, (na, n) in enumerate(spec)]
+
+
+@pytest.mark.parametrize("precision,scheme", [(1, 2), (1, 1), (0, 2)])
+def test_batch_equals_single_solves_bitwise(npb, precision, scheme):
+    """Each batched energy is the single-grid npb_energy value bit for bit (same kernels, same
+    shapes; legs of equal-size grids share launches), and a second call replays the graph."""
+    c = npb.npb_ctx_create(0, 0)
+    try:
+        grids = [npb.npb_grid_create(c, p) for p in _mols()]
+        try:
+            o = npb.make_opts(0.4, 0.04, 6, scheme=scheme, precision=precision)
+            single = [npb.npb_energy(g, o) for g in grids]
+            batch = npb.npb_energy_batch(grids, o)
+            again = npb.npb_energy_batch(grids, o)
+            assert batch == single
+            assert again == single
+            sub = npb.npb_energy_batch(grids[1:4], o)  # a different composition, its own plan
+            assert sub == single[1:4]
+        finally:
+            for g in grids:
+                npb.npb_grid_destroy(g)
+    finally:
+        npb.npb_ctx_destroy(c)
+
+
+def test_batch_matches_oracle(npb, O):
+    """FP32 batch against the FP64 oracle, molecule by molecule (1e-4 relative dG)."""
+    mols = _mols()[:3]
+    c = npb.npb_ctx_create(0, 0)
+    try:
+        grids = [npb.npb_grid_create(c, p) for p in mols]
+        try:
+            dg = npb.npb_energy_batch(grids, npb.make_opts(0.4, 0.04, 6, precision=1))
+        finally:
+            for g in grids:
+                npb.npb_grid_destroy(g)
+    finally:
+        npb.npb_ctx_destroy(c)
+    for p, v in zip(mols, dg):
+        ref = O.energy(p, 10.0, 6)
+        assert abs(v - ref) <= 1e-4 * abs(ref), (v, ref)
+
+
+def test_batch_after_destroy_and_invalid(npb):
+    c = npb.npb_ctx_create(0, 0)
+    try:
+        mols = _mols()
+        grids = [npb.npb_grid_create(c, p) for p in mols]
+        o = npb.make_opts(0.4, 0.04, 4, precision=1)
+        ref = npb.npb_energy_batch(grids, o)
+        npb.npb_grid_destroy(grids[0])  # drops the cached plan that names it
+        rest = grids[1:]
+        assert npb.npb_energy_batch(rest, o) == ref[1:]
+        g_new = npb.npb_grid_create(c, mols[0])  # may reuse the freed address
+        assert npb.npb_energy_batch([g_new] + rest, o) == ref
+        with pytest.raises(npb.NpbError):
+            npb.npb_energy_batch([rest[0], rest[0]], o)
+        with pytest.raises(npb.NpbError):
+            npb.npb_energy_batch([], o)
+        for g in [g_new] + rest:
+            npb.npb_grid_destroy(g)
+    finally:
+        npb.npb_ctx_destroy(c)
