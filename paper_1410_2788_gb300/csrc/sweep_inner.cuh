@@ -94,7 +94,9 @@ __device__ __forceinline__ void inner_ends(float fa, float fb, float fc, float f
     F = (fd - fa * Ep - fc * E) * ifb;
 }
 
-template <int DIR, int TX, int SEG, int L>
+// TABLE: the legs' tensor maps and constants come from the device-memory table P.table (any number
+// of legs of one grid size) instead of the launch's inline arrays (up to kTmaMaxLegs legs).
+template <int DIR, int TX, int SEG, int L, bool TABLE>
 __global__ void __launch_bounds__(TX *SEG, (768 / (TX * SEG)) > 0 ? 768 / (TX * SEG) : 1)
     sweep_inner_kernel(const __grid_constant__ TmaLaunch P, int flags) {
     using T = float;
@@ -121,10 +123,18 @@ __global__ void __launch_bounds__(TX *SEG, (768 / (TX * SEG)) > 0 ? 768 / (TX * 
     off += tma_align((size_t)(TX * SEG + 2 * kRows) * 16 + (size_t)TX * SEG * 4);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + off);
     int4 *tinfo = reinterpret_cast<int4 *>(bar + 2);  // (leg, a, b) of the tile in each stage
-    // a leg's tensor maps and constants: inline in the launch, or in the device-memory leg table
-    auto umap = [&](int leg) -> const CUtensorMap * { return P.table ? &P.table[leg].umap : &P.umap[leg]; };
-    auto mmap = [&](int leg) -> const CUtensorMap * { return P.table ? &P.table[leg].mmap : &P.mmap[leg]; };
-    auto legp = [&](int leg) -> const LegDev & { return P.table ? P.table[leg].dev : P.legs[leg]; };
+    auto legp = [&](int leg) -> const LegDev & {
+        if constexpr (TABLE) return P.table[leg].dev;
+        else return P.legs[leg];
+    };
+    auto umap = [&](int leg) -> const CUtensorMap * {
+        if constexpr (TABLE) return &P.table[leg].umap;
+        else return &P.umap[leg];
+    };
+    auto mmap = [&](int leg) -> const CUtensorMap * {
+        if constexpr (TABLE) return &P.table[leg].mmap;
+        else return &P.mmap[leg];
+    };
     for (int i = tid; i < 2 * kRows; i += TX * SEG) {  // identity rows; the margins are never written again
         fbuf[TX * SEG + i] = make_float4(0.f, 1.f, 0.f, 0.f);
     }

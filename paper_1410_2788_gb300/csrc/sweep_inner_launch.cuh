@@ -2,6 +2,7 @@
 #pragma once
 #include <algorithm>
 #include <map>
+#include <utility>
 #include <mutex>
 
 #include "sweep_inner.cuh"
@@ -19,17 +20,18 @@ static cudaError_t launch_inner_shape(const TmaLaunch &P, const TmaGeom &g, int 
     const size_t smem = inner_smem_bytes<TX, SEG>(DIR, g.rows, g.nload, g.sx, g.mwpr);
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
     if (DIR != DIR_X && g.nload > 1 && tma_data_box_bytes(g.rows, TX) % 128) return cudaErrorInvalidValue;
-    auto kern = sweep_inner_kernel<DIR, TX, SEG, L>;
+    const bool table = P.table != nullptr;
+    auto kern = table ? sweep_inner_kernel<DIR, TX, SEG, L, true> : sweep_inner_kernel<DIR, TX, SEG, L, false>;
     static std::mutex mu;
-    static std::map<size_t, int> occ;
+    static std::map<std::pair<size_t, bool>, int> occ;
     int per_sm = 0;
     {
         std::lock_guard<std::mutex> lk(mu);
-        auto it = occ.find(smem);
+        auto it = occ.find({smem, table});
         if (it == occ.end()) {
             cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX * SEG, smem);
             if (e != cudaSuccess) return e;
-            occ[smem] = per_sm;
+            occ[{smem, table}] = per_sm;
         } else {
             per_sm = it->second;
         }
@@ -51,16 +53,21 @@ static cudaError_t launch_inner_dir(TmaLaunch &P, const TmaGeom &g, int flags, S
     return cudaErrorInvalidValue;
 }
 
+template <typename K>
+static cudaError_t prepare_inner_kernel(K kern) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    return e;
+}
+
 template <int DIR, int TX>
 static cudaError_t prepare_inner_dir() {
     cudaError_t e = cudaSuccess;
 #define NPB_INNER_PREP(SEG_, L_)                                                                                  \
     if (e == cudaSuccess)                                                                                      \
-        e = cudaFuncSetAttribute(sweep_inner_kernel<DIR, TX, SEG_, L_>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                 200 * 1024);                                                                  \
-    if (e == cudaSuccess)                                                                                      \
-        e = cudaFuncSetAttribute(sweep_inner_kernel<DIR, TX, SEG_, L_>,                                           \
-                                 cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+        e = prepare_inner_kernel(sweep_inner_kernel<DIR, TX, SEG_, L_, false>);                                \
+    if (e == cudaSuccess) e = prepare_inner_kernel(sweep_inner_kernel<DIR, TX, SEG_, L_, true>);
     if constexpr (TX == 8) { NPB_INNER_SEGS_X(NPB_INNER_PREP) } else { NPB_INNER_SEGS_YZ(NPB_INNER_PREP) }
 #undef NPB_INNER_PREP
     return e;
