@@ -28,6 +28,10 @@ namespace npb {
 // tile with more than kSrcRegs * threads entries reads the rest when they are applied.
 constexpr int kSrcRegs = 2;
 
+// Shared-memory stages of the tile pipeline: tile t+k*grid is in flight while tile t is solved,
+// k < kInnerStages.
+constexpr int kInnerStages = 2;
+
 // Largest PCR stride for SEG segments (the highest power of two below SEG).
 template <int SEG>
 __host__ __device__ constexpr int pcr_top() {
@@ -48,7 +52,7 @@ __host__ __device__ __forceinline__ size_t inner_smem_bytes(int dir, int rows, i
     const size_t data = dir == DIR_X ? (size_t)TX * sx * 4 : (size_t)nload * tma_data_box_bytes(rows, TX);
     const size_t mask = (size_t)TX * mwpr * 4;
     const size_t red = (size_t)(TX * SEG + 2 * pcr_rows<TX, SEG>()) * 16 + (size_t)TX * SEG * 4;
-    return 128 + 2 * (tma_align(data) + tma_align(mask)) + tma_align(red) + 64;  // + barriers, tile indices
+    return 128 + kInnerStages * (tma_align(data) + tma_align(mask)) + tma_align(red) + 128;  // + barriers, tile indices
 }
 
 // The segment ends of one line: segment s contributes its F row (fa E_{s-1} + fb F_s + fc E_s = fd)
@@ -111,18 +115,19 @@ __global__ void __launch_bounds__(TX *SEG, (768 / (TX * SEG)) > 0 ? 768 / (TX * 
     // stage s: data at base + s * stage, mask after it (selected, not indexed: no local memory)
     const size_t base = (128 - (smem_addr(smem_raw) & 127u)) & 127u;
     const size_t stage = tma_align(data_b) + tma_align(mask_b);
-    auto data = [&](int s) { return reinterpret_cast<T *>(smem_raw + base + (s ? stage : 0)); };
+    constexpr int NS = kInnerStages;
+    auto data = [&](int s) { return reinterpret_cast<T *>(smem_raw + base + (size_t)s * stage); };
     auto msk = [&](int s) {
-        return reinterpret_cast<uint32_t *>(smem_raw + base + (s ? stage : 0) + tma_align(data_b));
+        return reinterpret_cast<uint32_t *>(smem_raw + base + (size_t)s * stage + tma_align(data_b));
     };
-    size_t off = base + 2 * stage;
+    size_t off = base + NS * stage;
     constexpr int kPad = pcr_top<SEG>() * TX, kRows = pcr_rows<TX, SEG>();
     float4 *fbuf = reinterpret_cast<float4 *>(smem_raw + off);
     float4 *pbuf = fbuf + TX * SEG + kPad;  // first real row of PCR buffer 0
     float *ebuf = reinterpret_cast<float *>(fbuf + TX * SEG + 2 * kRows);
     off += tma_align((size_t)(TX * SEG + 2 * kRows) * 16 + (size_t)TX * SEG * 4);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + off);
-    int4 *tinfo = reinterpret_cast<int4 *>(bar + 2);  // (leg, a, b) of the tile in each stage
+    int4 *tinfo = reinterpret_cast<int4 *>(bar + 4);  // (leg, a, b) of the tile in each stage
     auto legp = [&](int leg) -> const LegDev & {
         if constexpr (TABLE) return P.table[leg].dev;
         else return P.legs[leg];
@@ -165,10 +170,10 @@ __global__ void __launch_bounds__(TX *SEG, (768 / (TX * SEG)) > 0 ? 768 / (TX * 
 
     int t = blockIdx.x, it = 0;
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int k = 0; k < NS; ++k) mbar_init(&bar[k], 1);
         fence_mbar_init();
-        if (t < total) issue(t, 0);
+        for (int k = 0; k + 1 < NS; ++k)
+            if (t + k * (int)gridDim.x < total) issue(t + k * gridDim.x, k);
     }
     __syncthreads();  // barriers initialised, the first tile's indices visible
 
@@ -205,17 +210,19 @@ __global__ void __launch_bounds__(TX *SEG, (768 / (TX * SEG)) > 0 ? 768 / (TX * 
     int2 sv[kSrcRegs];
     int cur_tb = 0, cur_te = 0;  // entries held in sv for the tile solved next (none for the first)
     for (; t < total; t += gridDim.x, ++it) {
-        const int s = it & 1;
+        const int s = it % NS, sn = (it + 1) % NS;
         const int tn = t + gridDim.x;
-        if (tid == 0 && tn < total) {
+        const int tq = t + (NS - 1) * gridDim.x;  // issued now into the stage stored last iteration
+        if (tid == 0 && tq < total) {
             bulk_wait_read_all();
-            issue(tn, s ^ 1);
+            issue(tq, (it + NS - 1) % NS);
         }
-        const bool got = __syncthreads_and(mbar_wait_bounded(&bar[s], (it >> 1) & 1));
+        const bool got = __syncthreads_and(mbar_wait_bounded(&bar[s], (it / NS) & 1));
         if (!got) {
             if (tid == 0) {
                 atomicExch(P.err, 1);
-                if (tn < total) mbar_wait_bounded(&bar[s ^ 1], ((it + 1) >> 1) & 1);
+                for (int k = 1; k < NS; ++k)  // the copies still in flight
+                    if (t + k * (int)gridDim.x < total) mbar_wait_bounded(&bar[(it + k) % NS], ((it + k) / NS) & 1);
                 bulk_wait_all();
             }
             return;
@@ -259,7 +266,7 @@ __global__ void __launch_bounds__(TX *SEG, (768 / (TX * SEG)) > 0 ? 768 / (TX * 
         // the next tile's charge entries: range now, entries after the local elimination
         const bool src_next = fuse_src && tn < total;
         int ntb = 0, nte = 0;
-        if (src_next) src_range(s ^ 1, ntb, nte);
+        if (src_next) src_range(sn, ntb, nte);
         // row n-2 of the line: move its face coupling eps u_{n-1} to the right-hand side (after
         // the inflowing nonlinear stage, so the flow sees the bare node value)
         if (nrem >= 1 && nrem <= L) {
@@ -329,7 +336,7 @@ __global__ void __launch_bounds__(TX *SEG, (768 / (TX * SEG)) > 0 ? 768 / (TX * 
             fa = T(0);
         }
         if (src_next) {
-            const int2 *ent = legp(tinfo[s ^ 1].x).ent_xq;
+            const int2 *ent = legp(tinfo[sn].x).ent_xq;
 #pragma unroll
             for (int r = 0; r < kSrcRegs; ++r) {
                 const int e = ntb + tid + r * NT;
