@@ -32,6 +32,28 @@ constexpr int kSrcRegs = 2;
 // k < kInnerStages.
 constexpr int kInnerStages = 2;
 
+// Packed FP32 pairs (sm_100 family): one instruction does two IEEE fma/mul, each lane rounded
+// exactly as the scalar operation, so results are bit-identical to the scalar code.
+__device__ __forceinline__ unsigned long long f2_pack(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long v, float &a, float &b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // Largest PCR stride for SEG segments (the highest power of two below SEG).
 template <int SEG>
 __host__ __device__ constexpr int pcr_top() {
@@ -294,7 +316,10 @@ __global__ void __launch_bounds__(TX *SEG, (768 / (TX * SEG)) > 0 ? 768 / (TX * 
             // row 0 (F) coefficients, then the forward elimination over rows 1 .. L-2 with x_0 = F
             const T em0 = eh(0), ep0 = eh(1);
             const T epc0 = (FULL || 1 < nrem) ? ep0 : T(0);
-            T em = ep0, h = T(1), ap = T(0), bp = T(1);
+            // (alpha, beta) of a row travel as one packed pair: (ap, bp) = ((al_k, 0) + em (ap, bp)) m
+            T em = ep0, h = T(1);
+            unsigned long long ab[L];
+            ab[0] = f2_pack(T(0), T(1));
 #pragma unroll
             for (int k = 1; k <= L - 2; ++k) {
                 const T ep = eh(k + 1);
@@ -302,10 +327,7 @@ __global__ void __launch_bounds__(TX *SEG, (768 / (TX * SEG)) > 0 ? 768 / (TX * 
                 const T m = fast_rcp(fmaf(em, h, T(1) + ep));
                 const T g = epc * m;
                 h = T(1) - g;
-                ap = fmaf(em, ap, al[k]) * m;
-                bp = em * bp * m;
-                al[k] = ap;
-                be[k] = bp;
+                ab[k] = f2_mul(f2_fma(f2_pack(em, em), ab[k - 1], f2_pack(al[k], T(0))), f2_pack(m, m));
                 ga[k] = g;
                 em = ep;
             }
@@ -313,10 +335,11 @@ __global__ void __launch_bounds__(TX *SEG, (768 / (TX * SEG)) > 0 ? 768 / (TX * 
 #pragma unroll
             for (int k = L - 3; k >= 1; --k) {
                 const T g = ga[k];
-                al[k] = fmaf(g, al[k + 1], al[k]);
-                be[k] = fmaf(g, be[k + 1], be[k]);
+                ab[k] = f2_fma(f2_pack(g, g), ab[k + 1], ab[k]);
                 ga[k] = g * ga[k + 1];
             }
+#pragma unroll
+            for (int k = 1; k <= L - 2; ++k) f2_unpack(ab[k], al[k], be[k]);
             const T emL = em, epL = eh(L);
             const T epcL = L < nrem ? epL : T(0);
             fa = -em0;
