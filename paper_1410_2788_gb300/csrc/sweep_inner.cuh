@@ -122,8 +122,15 @@ __device__ __forceinline__ void inner_ends(float fa, float fb, float fc, float f
 
 // TABLE: the legs' tensor maps and constants come from the device-memory table P.table (any number
 // of legs of one grid size) instead of the launch's inline arrays (up to kTmaMaxLegs legs).
+// Resident blocks asked of the register allocator: 24 warps per SM for blocks below 256 threads;
+// 32 warps (64 registers) for 256 threads and more, where it measured faster despite a few spills.
+template <int NT>
+constexpr int inner_min_blocks() {
+    return NT >= 256 ? (1024 / NT > 0 ? 1024 / NT : 1) : (768 / NT > 0 ? 768 / NT : 1);
+}
+
 template <int DIR, int TX, int SEG, int L, bool TABLE>
-__global__ void __launch_bounds__(TX *SEG, (768 / (TX * SEG)) > 0 ? 768 / (TX * SEG) : 1)
+__global__ void __launch_bounds__(TX *SEG, inner_min_blocks<TX * SEG>())
     sweep_inner_kernel(const __grid_constant__ TmaLaunch P, int flags) {
     using T = float;
     static_assert(L >= 3 && L <= 29 && (L & 1), "odd segment length (conflict-free rows); L+2 node bits fit a word");
