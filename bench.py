@@ -80,54 +80,83 @@ def aggregate(local_seconds: float, local_units: float, world: int, group=None):
 
 # ----------------------------------------------------------------------------- clocks
 class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples every 20 ms, time-stamped on the host.  Started
+    before the warm-up so that the sampler is running when the timed region begins; `stop` keeps
+    the samples inside the timed window (`mark_start`/`mark_end`), or the two that bracket it when
+    the window is shorter than the sampling period."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = None
+        self.samples = []
+        self.t0 = self.t1 = None
 
     def start(self):
+        import threading
+
         try:
-            fd, self.path = tempfile.mkstemp(suffix=".csv")
-            os.close(fd)
-            self.out = open(self.path, "w")
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
-                 "-i", str(self.gpu)], stdout=self.out, stderr=subprocess.DEVNULL)
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "20",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True, bufsize=1)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+
+        def reader():
+            for line in self.proc.stdout:
+                self.samples.append((time.perf_counter(), line))
+
+        self.th = threading.Thread(target=reader, daemon=True)
+        self.th.start()
+
+    def mark_start(self):
+        self.t0 = time.perf_counter()
+
+    def mark_end(self):
+        self.t1 = time.perf_counter()
 
     def stop(self):
         if not self.proc:
             return None
+        time.sleep(0.05)  # one more sample after the window
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        self.out.close()
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        self.th.join(timeout=2)
+        rows = []
+        for t, line in self.samples:
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
             try:
-                sm.append(float(f[1]))
-                smax.append(float(f[2]))
+                rows.append((t, float(f[1]), float(f[2]), f[5:9]))
             except ValueError:
                 continue
-            for nm, v in zip(names, f[5:9]):
+        if not rows:
+            return None
+        t0 = self.t0 if self.t0 is not None else rows[0][0]
+        t1 = self.t1 if self.t1 is not None else rows[-1][0]
+        inside = [r for r in rows if t0 <= r[0] <= t1]
+        window = "inside the timed region"
+        if not inside:  # the region is shorter than the sampling period: the bracketing samples
+            before = [r for r in rows if r[0] < t0][-1:]
+            after = [r for r in rows if r[0] > t1][:1]
+            inside = before + after
+            window = "bracketing the timed region"
+        reasons = set()
+        for r in inside:
+            for nm, v in zip(self.NAMES, r[3]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
-        os.unlink(self.path)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+                "reasons": sorted(reasons), "samples": len(inside), "window": window,
+                "timed_region_s": round(t1 - t0, 4)}
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -384,6 +413,8 @@ def run_ours(args):
             torch.cuda.synchronize()
         return [x.elapsed_time(y) for x, y in ms], dg
 
+    clocks = ClockSampler(local)
+    clocks.start()  # running before the timed region begins
     with torch.cuda.stream(stream):
         for _ in range(max(args.warmup, 3)):
             step(opts)
@@ -391,15 +422,15 @@ def run_ours(args):
     torch.cuda.synchronize()
 
     # ---- headline: K steps of the FP32-sweep path
-    clocks = ClockSampler(local)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    clocks.mark_start()
     wall0 = time.perf_counter()
     step_ms, dg = timed(opts, args.steps)
     wall = time.perf_counter() - wall0
     torch.cuda.synchronize()
+    clocks.mark_end()
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
