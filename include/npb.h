@@ -183,6 +183,17 @@ int npb_energy_batch(npb_grid *const *grids, int32_t n_grids, const npb_opts *op
  * (dimensionless), nz*ny*nx of them, x fastest.  n_elems must equal nx*ny*nz. */
 int npb_potential(npb_grid *grid, int32_t leg, double *host_out, size_t n_elems);
 
+/* n_steps LOD steps (Sec. 3.1, opts->scheme) of leg `leg` from a caller-given state, the
+ * pseudo-time run of Eq. (TimeDepNPB) with that leg's medium, eps at half points (opts->eps_mode)
+ * and tau = dt/alpha (halved for the *_HALF legs).  u_inout: nz*ny*nx FP64 values of u, x
+ * fastest; its interior is the initial value and its faces the Dirichlet data, which no stage
+ * changes; the final state is copied back into it.  source (same layout, may be NULL) is a dense
+ * source density rho: stage S then adds tau*rho at the interior nodes in place of the molecule's
+ * point charges (the manufactured-solution benchmark of Sec. 4.1, Eqs. NPB_analytical_1/2);
+ * with NULL the step is the usual one with the charges.  n_elems must equal nx*ny*nz. */
+int npb_lod_run(npb_grid *grid, const npb_opts *opts, int32_t leg, int32_t n_steps, double *u_inout,
+                const double *source, size_t n_elems);
+
 /* Row-level access to single LOD stages: load the dense FP64 field u_inout (nz*ny*nx)
  * into leg `leg`'s state (rounded to opts->precision), apply stage `op` (NPB_OP_*)
  * with that leg's medium and tau = dt/alpha (halved for the *_HALF legs), and copy the

@@ -81,6 +81,7 @@ SIGNATURES = {
     "npb_lod_solve": (_I, [_V, ctypes.POINTER(npb_opts), _I32, ctypes.c_double]),
     "npb_energy": (_I, [_V, ctypes.POINTER(npb_opts), _dp]),
     "npb_energy_batch": (_I, [ctypes.POINTER(_V), _I32, ctypes.POINTER(npb_opts), ctypes.POINTER(ctypes.c_double)]),
+    "npb_lod_run": (_I, [_V, ctypes.POINTER(npb_opts), _I32, _I32, _dp, _dp, _SZ]),
     "npb_potential": (_I, [_V, _I32, _dp, _SZ]),
     "npb_apply": (_I, [_V, ctypes.POINTER(npb_opts), _I32, _I32, _dp, _SZ]),
     "npb_grid_export": (_I, [_V, _I32, _V, _SZ]),
@@ -224,6 +225,16 @@ def npb_energy_batch(grids, opts: npb_opts) -> list:
     out = (ctypes.c_double * n)()
     _check(load_library().npb_energy_batch(arr, n, ctypes.byref(opts), out))
     return list(out)
+
+
+def npb_lod_run(grid: int, opts: npb_opts, leg: int, n_steps: int, u: np.ndarray, source=None) -> np.ndarray:
+    """n LOD steps of one leg from the dense FP64 state u (faces = Dirichlet data); with `source`
+    (dense FP64 rho) stage S adds tau*rho instead of the molecule's charges.  Returns the new state."""
+    out = np.ascontiguousarray(u, dtype=np.float64).copy()
+    src = None if source is None else np.ascontiguousarray(source, dtype=np.float64)
+    _check(load_library().npb_lod_run(grid, ctypes.byref(opts), leg, n_steps, out.ctypes.data_as(_dp),
+                                      None if src is None else src.ctypes.data_as(_dp), out.size))
+    return out
 
 
 def npb_potential(grid: int, leg: int, shape) -> np.ndarray:

@@ -936,6 +936,76 @@ extern "C" int npb_apply(npb_grid *g, const npb_opts *o, int32_t leg, int32_t op
     return grid_check_err(g, st, 0);
 }
 
+// n LOD steps of one leg from a caller-given state, optionally with a dense source in place of the
+// molecule's charges (the manufactured-solution benchmark of Sec. 4.1).
+extern "C" int npb_lod_run(npb_grid *g, const npb_opts *o, int32_t leg, int32_t n_steps, double *u_inout,
+                           const double *source, size_t n_elems) {
+    if (!g || !u_inout) return fail(NPB_EINVAL, "grid/u_inout is NULL");
+    int rc = check_opts(o);
+    if (rc) return rc;
+    if (leg < 0 || leg > 3) return fail(NPB_EINVAL, "unknown leg %d", leg);
+    if (n_steps < 0) return fail(NPB_EINVAL, "n_steps < 0");
+    const size_t total = (size_t)g->geo.nx * g->geo.ny * g->geo.nz;
+    if (n_elems != total) return fail(NPB_EINVAL, "n_elems %zu != nx*ny*nz %zu", n_elems, total);
+    CU(cudaSetDevice(g->ctx->device));
+    cudaStream_t st = g->ctx->stream;
+    if ((rc = grid_prepare(g, o, st))) return rc;
+    const int slot = kLegSlot[leg];
+    const int prec = o->precision;
+    void *u = g->d_u[prec][slot];
+    const size_t sbytes = state_bytes(&g->geo.nx, prec);
+    void *tmp = nullptr, *src = nullptr;
+    if ((rc = g->ctx->alloc(&tmp, total * sizeof(double)))) return rc;
+    if (source && (rc = g->ctx->alloc(&src, sbytes))) {
+        g->ctx->release(tmp, total * sizeof(double));
+        return rc;
+    }
+    auto done = [&](int r) {
+        cudaStreamSynchronize(st);
+        g->ctx->release(tmp, total * sizeof(double));
+        if (src) g->ctx->release(src, sbytes);
+        return r;
+    };
+    cudaError_t e = cudaSuccess;
+    if (source) {  // tau * rho in the state's precision and layout
+        const bool half = leg == NPB_LEG_SOLVENT_HALF || leg == NPB_LEG_VACUUM_HALF;
+        const double tau = (half ? 0.5 : 1.0) * o->dt / o->alpha;
+        std::vector<double> scaled(source, source + total);
+        for (double &v : scaled) v *= tau;
+        e = cudaMemcpyAsync(tmp, scaled.data(), total * sizeof(double), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(src, 0, sbytes, st);
+        if (e == cudaSuccess) e = pad_state(prec, g->geo, (const double *)tmp, src, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // `scaled` goes out of scope
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, u_inout, total * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(u, 0, sbytes, st);
+    if (e == cudaSuccess) e = pad_state(prec, g->geo, (const double *)tmp, u, st);
+    if (e != cudaSuccess) return done(fail(NPB_ECUDA, "npb_lod_run failed: %s", cudaGetErrorString(e)));
+    const int n_dir[3] = {g->geo.nx, g->geo.ny, g->geo.nz};
+    for (int s = 0; s < n_steps; ++s) {
+        if (!source) {
+            if ((rc = run_step(g, prec, o->scheme, slot, 1, st))) return done(rc);
+            continue;
+        }
+        // the stages of Sec. 3.1 with S = u + tau rho: LODIE2 S, X, Y, Z, N; LODIE1 N, X, Y, Z, S
+        if (o->scheme == NPB_LODIE2 && (e = launch_add_interior(prec, g->geo, src, u, st)) != cudaSuccess) break;
+        for (int d = 0; d < 3 && e == cudaSuccess; ++d) {
+            int flags = 0;
+            if (d == 0 && o->scheme == NPB_LODIE1) flags = FUSE_PRE_NL;
+            if (d == 2 && o->scheme == NPB_LODIE2) flags = FUSE_POST_NL;
+            e = launch_dir(g, prec, d, shape_for(g->ctx, prec, d, n_dir[d]), slot, 1, flags, st);
+        }
+        if (e == cudaSuccess && o->scheme == NPB_LODIE1) e = launch_add_interior(prec, g->geo, src, u, st);
+        if (e != cudaSuccess) break;
+    }
+    if (e == cudaSuccess) e = unpad_state(prec, g->geo, u, (double *)tmp, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(u_inout, tmp, total * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return done(fail(NPB_ECUDA, "npb_lod_run failed: %s", cudaGetErrorString(e)));
+    done(0);
+    return grid_check_err(g, st, 0);
+}
+
 extern "C" int npb_grid_export(npb_grid *g, int32_t what, void *host_out, size_t n_elems) {
     if (!g || !host_out) return fail(NPB_EINVAL, "grid/host_out is NULL");
     const size_t total = (size_t)g->geo.nx * g->geo.ny * g->geo.nz;

@@ -78,5 +78,8 @@ cudaError_t launch_nonlinear(int prec, const LegDev *legs_dev, int n_legs, int n
                              cudaStream_t st);
 cudaError_t launch_source(int prec, const LegDev *legs_dev, int n_legs, int ny, int nz,
                           cudaStream_t st);
+struct GridGeom;
+// u += src at the interior nodes of a padded state (dense source stage).
+cudaError_t launch_add_interior(int prec, const GridGeom &g, const void *src, void *u, cudaStream_t st);
 
 }  // namespace npb

@@ -3,11 +3,15 @@
 //   nonlinear   Eq. (ana3) at every interior solvent node (used on its own by the
 //               row-level interface; inside a step it is fused into a sweep)
 //   source      Eq. (LODIE1_5): u += tau Q over the charge entries (LODIE1 ends on it)
+//   add         u += tau rho over the interior, for a dense source density (Sec. 4.1)
 //   energy      Eqs. (rich) and (deltaG3): the FP64 charge-weighted sum over the
 //               charge nodes of the Richardson-combined solvent minus vacuum potential,
 //               reduced in a fixed order (one block, fixed tree), so the value does not
 //               depend on scheduling.
+#include <algorithm>
+
 #include "npb_internal.cuh"
+#include "setup_kernels.cuh"
 #include "sweep_kernel.cuh"
 
 namespace npb {
@@ -53,6 +57,28 @@ cudaError_t launch_nonlinear(int prec, const LegDev *legs, int n_legs, int nx, i
     dim3 grid(152 * 4, 1, n_legs);
     if (prec == 0) k_nonlinear<double><<<grid, 256, 0, st>>>(legs);
     else k_nonlinear<float><<<grid, 256, 0, st>>>(legs);
+    return cudaGetLastError();
+}
+
+// u += s at interior nodes, s a padded array in the state's layout (a dense source tau*rho).
+template <typename T>
+__global__ void k_add_interior(GridGeom g, const T *__restrict__ src, T *__restrict__ u) {
+    const int64_t total = (int64_t)g.nz * g.ny * g.pitch;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(p % g.pitch);
+        const int64_t r = p / g.pitch;
+        const int j = (int)(r % g.ny), k = (int)(r / g.ny);
+        if (i >= 1 && i <= g.nx - 2 && j >= 1 && j <= g.ny - 2 && k >= 1 && k <= g.nz - 2) u[p] += src[p];
+    }
+}
+
+cudaError_t launch_add_interior(int prec, const GridGeom &g, const void *src, void *u, cudaStream_t st) {
+    const int64_t total = (int64_t)g.nz * g.ny * g.pitch;
+    const int t = 256;
+    const int b = (int)std::min<int64_t>((total + t - 1) / t, 152 * 16);
+    if (prec == 0) k_add_interior<double><<<b, t, 0, st>>>(g, (const double *)src, (double *)u);
+    else k_add_interior<float><<<b, t, 0, st>>>(g, (const float *)src, (float *)u);
     return cudaGetLastError();
 }
 
