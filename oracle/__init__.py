@@ -13,6 +13,8 @@ legs into the solvation energy:
                   (Sec. 2.1, Eqs. RhoEq / DebyeHuckel / BoundaryCond, Sec. 3.1)
   * `lod_leg`   - one pseudo-time integration from u = 0 (Sec. 2.2, LODIE2 of Sec. 3.1)
   * `energy`    - Eq. (deltaG3) with Richardson extrapolation Eq. (rich) (Sec. 5.3)
+  * `vacuum_fft` - phi_0^FFT of Eq. (deltaG2): the vacuum Poisson problem solved directly with
+                  the sine transform (Sec. 5.1); `energy_fft` - Eq. (deltaG2)
 
 Readings where the paper is silent (all stated in the design doc):
   * C = e_c^2/(k_B T) = 332.0637 / 0.592183 A (Coulomb constant over kT at 298 K);
@@ -284,6 +286,47 @@ def energy(problem, tau: float, n_steps: int, richardson: bool = True, scheme: i
     if return_legs:
         return dg, legs, st_s
     return dg
+
+
+# ---------------------------------------------------------------- FFT vacuum potential (Sec. 5.1, 5.3)
+def poisson_dst(f: np.ndarray, h: float) -> np.ndarray:
+    """Solve -Delta_h v = f on the interior nodes of a box with zero Dirichlet faces, Delta_h the
+    central 7-point difference: the sine vectors sin(pi k i / (N+1)) diagonalise it with eigenvalue
+    sum_d (2 - 2 cos(pi k_d / (N_d + 1))) / h^2, so v = DST-I^-1 (DST-I(f) / lambda) (the fast
+    Poisson solver the paper names for phi_0; scipy's type-1 DST is the library step)."""
+    from scipy.fft import dstn, idstn
+
+    lam = np.zeros(f.shape)
+    for axis, n in enumerate(f.shape):
+        k = np.arange(1, n + 1, dtype=np.float64)
+        shape = [1, 1, 1]
+        shape[axis] = n
+        lam = lam + ((2.0 - 2.0 * np.cos(math.pi * k / (n + 1))) / (h * h)).reshape(shape)
+    return idstn(dstn(f, type=1) / lam, type=1)
+
+
+def vacuum_fft(problem) -> np.ndarray:
+    """phi_0^FFT of Eq. (deltaG2) as u (dimensionless): the direct solution of the vacuum Poisson
+    problem eps_in Delta_h u + rho = 0 with the vacuum Dirichlet faces.  The face values move to the
+    right-hand side (each interior node adds its face neighbours / h^2), leaving zero faces."""
+    st = setup(problem, VACUUM)
+    u = st.u0.copy()
+    h = problem.h
+    nb = (u[2:, 1:-1, 1:-1] + u[:-2, 1:-1, 1:-1] + u[1:-1, 2:, 1:-1] + u[1:-1, :-2, 1:-1] +
+          u[1:-1, 1:-1, 2:] + u[1:-1, 1:-1, :-2])  # zero at interior neighbours of u0
+    f = st.rho[1:-1, 1:-1, 1:-1] / problem.eps_in + nb / (h * h)
+    u[1:-1, 1:-1, 1:-1] = poisson_dst(f, h)
+    return u
+
+
+def energy_fft(problem, tau: float, n_steps: int, richardson: bool = True, scheme: int = LODIE2,
+               eps_mode: str = "harmonic") -> float:
+    """Eq. (deltaG2): the LOD solvent potential (Richardson-combined) against phi_0^FFT."""
+    st_s = setup(problem, SOLVENT, eps_mode)
+    us = lod_leg(problem, SOLVENT, tau, n_steps, scheme, st=st_s)
+    if richardson:
+        us = 2.0 * lod_leg(problem, SOLVENT, 0.5 * tau, 2 * n_steps, scheme, st=st_s) - us
+    return delta_g(st_s.qt, us, vacuum_fft(problem))
 
 
 def born_closed_form(q: float, radius: float, eps_in: float, eps_out: float) -> float:

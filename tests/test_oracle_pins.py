@@ -357,3 +357,61 @@ def test_lod_steady_state_tends_to_discrete_npb_solution(oracle_lib):
     ere = np.abs(2 * legs[0.01] - legs[0.02] - ue).max()
     assert 1.75 < e1 / e2 < 2.25, (e1, e2)
     assert ere < 0.15 * e2
+
+
+# --------------------------------------------------------------------------- FFT vacuum potential
+def _tiny_problem(n=(9, 8, 7)):
+    return I.Problem(xyz=np.array([[2.1, 1.7, 1.6], [1.8, 2.0, 1.4]]), q=np.array([0.6, -0.9]),
+                     radius=np.array([1.6, 1.5]), eps_in=2.0, eps_out=80.0, kappa2=0.84, h=0.5, n=n,
+                     origin=(0.0, 0.0, 0.0))
+
+
+def test_poisson_dst_discrete_eigenvector(oracle_lib):
+    """A product of sine vectors is an eigenvector of -Delta_h with the stated eigenvalue."""
+    nz, ny, nx, h = 6, 5, 7, 0.3
+    k = (2, 3, 1)
+    z, y, x = np.meshgrid(np.arange(1, nz + 1), np.arange(1, ny + 1), np.arange(1, nx + 1), indexing="ij")
+    f = np.sin(math.pi * k[0] * z / (nz + 1)) * np.sin(math.pi * k[1] * y / (ny + 1)) * np.sin(math.pi * k[2] * x / (nx + 1))
+    lam = sum((2 - 2 * math.cos(math.pi * kk / (nn + 1))) / h ** 2 for kk, nn in zip(k, (nz, ny, nx)))
+    assert np.allclose(oracle_lib.poisson_dst(f, h), f / lam, rtol=1e-12, atol=1e-14)
+
+
+def test_vacuum_fft_equals_dense_solve(oracle_lib):
+    """phi_0^FFT = the dense LU solution of eps_in Delta_h u + rho = 0 with the vacuum faces."""
+    p = _tiny_problem()
+    u = oracle_lib.vacuum_fft(p)
+    st = oracle_lib.setup(p, oracle_lib.VACUUM)
+    nz, ny, nx = u.shape
+    idx = -np.ones(u.shape, dtype=int)
+    inner = [(k, j, i) for k in range(1, nz - 1) for j in range(1, ny - 1) for i in range(1, nx - 1)]
+    for m, c in enumerate(inner):
+        idx[c] = m
+    A = np.zeros((len(inner), len(inner)))
+    b = np.zeros(len(inner))
+    h2 = p.h * p.h
+    for m, (k, j, i) in enumerate(inner):
+        A[m, m] = 6.0 * p.eps_in / h2
+        b[m] = st.rho[k, j, i]
+        for dk, dj, di in [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)]:
+            c = (k + dk, j + dj, i + di)
+            if idx[c] >= 0:
+                A[m, idx[c]] -= p.eps_in / h2
+            else:
+                b[m] += p.eps_in / h2 * st.u0[c]
+    v = np.linalg.solve(A, b)
+    ref = st.u0.copy()
+    for m, c in enumerate(inner):
+        ref[c] = v[m]
+    assert np.max(np.abs(u - ref)) <= 1e-11 * np.max(np.abs(ref))
+
+
+def test_vacuum_lod_leg_tends_to_fft(oracle_lib):
+    """The vacuum LOD leg's steady state is the same Poisson problem up to the O(tau) splitting
+    error (Sec. 3.1): its distance to phi_0^FFT halves with tau."""
+    p = _tiny_problem((13, 12, 11))
+    ref = oracle_lib.vacuum_fft(p)
+    d = []
+    for tau in (0.02, 0.01, 0.005):
+        u = oracle_lib.lod_leg(p, oracle_lib.VACUUM, tau, int(round(40.0 / tau)))
+        d.append(np.max(np.abs(u - ref)) / np.max(np.abs(ref)))
+    assert d[2] < 0.05 and all(1.6 < a / b < 2.4 for a, b in zip(d, d[1:])), d
