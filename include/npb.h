@@ -67,6 +67,11 @@ extern "C" {
 #define NPB_LEG_SOLVENT_HALF 1
 #define NPB_LEG_VACUUM_TAU 2
 #define NPB_LEG_VACUUM_HALF 3
+/* npb_potential() only: phi_0^FFT of Eq. (deltaG2), the vacuum potential by the direct (sine
+ * transform) Poisson solve; and the recovered potential phi_m^LOD + phi_0^LOD - phi_0^FFT of
+ * Sec. 5.3 (each LOD potential Richardson-combined when the last solve used Richardson). */
+#define NPB_LEG_VACUUM_FFT 4
+#define NPB_LEG_RECOVERED 5
 
 /* Single stages for npb_apply() (row-level checks of one LOD stage). */
 #define NPB_OP_SOURCE 0     /* u += tau Q at interior charge nodes        Eq. (LODIE1_5) */
@@ -104,14 +109,16 @@ typedef struct {
 } npb_problem;
 
 /* Pseudo-time options: tau = dt/alpha; the Richardson leg uses dt/2 and 2 n_steps
- * (Sec. 5.3).  richardson and vacuum_recovery are 0/1 flags; npb_energy() needs
- * vacuum_recovery = 1 (the FFT vacuum potential of Eq. deltaG2 is not provided). */
+ * (Sec. 5.3).  richardson and vacuum_recovery are 0/1 flags.  vacuum_recovery = 1: the
+ * vacuum potential is the LOD vacuum legs' (Eq. deltaG3, the paper's RE+V); 0: it is the
+ * direct Poisson solution phi_0^FFT (Eq. deltaG2), and only the solvent legs run
+ * (npb_energy only; npb_energy_batch and npb_submit need 1). */
 typedef struct {
     double dt, alpha;
     int32_t n_steps;
     int32_t scheme;           /* NPB_LODIE2 (default) or NPB_LODIE1                   */
     int32_t richardson;       /* 1: RE of Eq. (rich)                                   */
-    int32_t vacuum_recovery;  /* 1: LOD vacuum legs of Eq. (deltaG3)                  */
+    int32_t vacuum_recovery;  /* 1: LOD vacuum legs of Eq. (deltaG3); 0: Eq. (deltaG2) */
     int32_t precision;        /* NPB_FP64 or NPB_FP32_SWEEP                            */
     int32_t eps_mode;         /* NPB_EPS_HARMONIC (default) or NPB_EPS_MIDPOINT        */
 } npb_opts;
@@ -179,7 +186,9 @@ int npb_energy(npb_grid *grid, const npb_opts *opts, double *dG_kcal_mol);
  * bounded device wait expired (all values are then unreliable). */
 int npb_energy_batch(npb_grid *const *grids, int32_t n_grids, const npb_opts *opts, double *dG_kcal_mol);
 
-/* Copy leg `leg` (NPB_LEG_*) of the last solve to host_out as dense FP64 values of u
+/* Copy leg `leg` (NPB_LEG_*) of the last solve -- or phi_0^FFT (NPB_LEG_VACUUM_FFT), or the
+ * recovered potential (NPB_LEG_RECOVERED, after a solve with vacuum_recovery = 1) -- to host_out
+ * as dense FP64 values of u
  * (dimensionless), nz*ny*nx of them, x fastest.  n_elems must equal nx*ny*nz. */
 int npb_potential(npb_grid *grid, int32_t leg, double *host_out, size_t n_elems);
 

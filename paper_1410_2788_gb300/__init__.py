@@ -29,6 +29,7 @@ NPB_LODIE1, NPB_LODIE2 = 1, 2
 NPB_FP64, NPB_FP32_SWEEP = 0, 1
 NPB_EPS_HARMONIC, NPB_EPS_MIDPOINT = 0, 1
 NPB_LEG_SOLVENT_TAU, NPB_LEG_SOLVENT_HALF, NPB_LEG_VACUUM_TAU, NPB_LEG_VACUUM_HALF = 0, 1, 2, 3
+NPB_LEG_VACUUM_FFT, NPB_LEG_RECOVERED = 4, 5  # npb_potential only
 NPB_OP_SOURCE, NPB_OP_SWEEP_X, NPB_OP_SWEEP_Y, NPB_OP_SWEEP_Z, NPB_OP_NONLINEAR, NPB_OP_STEP = range(6)
 NPB_EXPORT_MASK, NPB_EXPORT_QTILDE, NPB_EXPORT_U0_SOLVENT, NPB_EXPORT_U0_VACUUM = range(4)
 

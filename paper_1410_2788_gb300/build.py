@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "libnpb.so")
 
 SOURCES = ["api.cu", "serve.cu", "setup_kernels.cu", "stage_kernels.cu", "sweep_f32.cu", "sweep_f64.cu",
            "tune.cu", "static_scratch.cu", "sweep_tma_f32.cu", "sweep_inner_x.cu", "sweep_inner_y.cu", "sweep_inner_z.cu",
-           "batch.cu"]
+           "batch.cu", "fft_vacuum.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
                 "-diag-suppress", "20040"]
@@ -61,7 +61,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     newest = max(os.path.getmtime(o) for o in objs)
     if force or not os.path.exists(LIB_PATH) or os.path.getmtime(LIB_PATH) < newest:
         tmp = LIB_PATH + f".tmp{os.getpid()}"
-        cmd = [_nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"]
+        cuda_lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(_nvcc()))), "lib64")
+        cmd = [_nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcufft", "-lpthread", "-Xlinker", "-rpath",
+                                                                 "-Xlinker", cuda_lib]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")

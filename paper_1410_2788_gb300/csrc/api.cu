@@ -48,7 +48,7 @@ cudaError_t prepare_sweep_f32();
 cudaError_t prepare_sweep_f64();
 cudaError_t launch_energy(int prec, const void *s_tau, const void *s_half, const void *v_tau,
                           const void *v_half, const int64_t *off, const double *qt, const int32_t *n_ent,
-                          int richardson, double *out, cudaStream_t st);
+                          int richardson, const double *vac, double *out, cudaStream_t st);
 
 // Shapes the line solver is instantiated for (kept in sync with NPB_SWEEP_SHAPES).
 static const SweepShape kShapes[] = {{16, 2, 17}, {16, 4, 9},   {16, 4, 17}, {16, 8, 9},
@@ -267,10 +267,6 @@ static int validate(const npb_problem *p, double origin[3]) {
     return 0;
 }
 
-static size_t state_bytes(const int n[3], int prec) {
-    const size_t pitch = (size_t)(n[0] + 31) / 32 * 32;
-    return pitch * n[1] * n[2] * (prec == NPB_FP64 ? 8 : 4);
-}
 
 extern "C" size_t npb_grid_footprint(const npb_problem *p, int32_t precision) {
     if (!p) return 0;
@@ -290,15 +286,6 @@ extern "C" size_t npb_grid_footprint(const npb_problem *p, int32_t precision) {
     return b;
 }
 
-template <typename T>
-static int galloc(npb_grid *g, T **p, size_t count) {
-    void *v = nullptr;
-    int rc = g->ctx->alloc(&v, count * sizeof(T));
-    if (rc) return rc;
-    g->allocs.push_back({v, count * sizeof(T)});
-    *p = static_cast<T *>(v);
-    return 0;
-}
 
 void npb::grid_free(npb_grid *g) {
     if (!g) return;
@@ -413,6 +400,7 @@ int npb::grid_setup(npb_grid *g, cudaStream_t st) {
     // face data are recomputed on their next use, only for the precision that uses them
     for (int m = 0; m < 2; ++m)
         for (int k = 0; k < 2; ++k) g->bc_valid[m][k] = false;
+    g->vac_fft_valid = false;
     return 0;
 }
 
@@ -739,7 +727,20 @@ int npb::enqueue_energy(npb_grid *g, const npb_opts *o, cudaStream_t st) {
     const int n = o->n_steps;
     const int legs_re[4] = {NPB_LEG_SOLVENT_TAU, NPB_LEG_SOLVENT_HALF, NPB_LEG_VACUUM_TAU, NPB_LEG_VACUUM_HALF};
     const int legs_plain[2] = {NPB_LEG_SOLVENT_TAU, NPB_LEG_VACUUM_TAU};
-    int rc = init_legs(g, prec, re ? legs_re : legs_plain, re ? 4 : 2, st);
+    int rc;
+    if (!o->vacuum_recovery) {  // Eq. (deltaG2): solvent legs only, phi_0^FFT for the vacuum
+        const int legs_s[2] = {NPB_LEG_SOLVENT_TAU, NPB_LEG_SOLVENT_HALF};
+        if ((rc = init_legs(g, prec, legs_s, re ? 2 : 1, st))) return rc;
+        const int s_tau = kLegSlot[NPB_LEG_SOLVENT_TAU], s_half = kLegSlot[NPB_LEG_SOLVENT_HALF];
+        for (int s = 0; s < n; ++s) {
+            if ((rc = run_step(g, prec, o->scheme, s_tau, 1, st))) return rc;
+            if (re && (rc = run_step(g, prec, o->scheme, s_half, 1, st))) return rc;
+        }
+        if (re)
+            for (int s = 0; s < n; ++s)
+                if ((rc = run_step(g, prec, o->scheme, s_half, 1, st))) return rc;
+    } else {
+    rc = init_legs(g, prec, re ? legs_re : legs_plain, re ? 4 : 2, st);
     if (rc) return rc;
     if (re) {
         // steps 1..n: all four legs (slots 0..3); steps n+1..2n: the dt/2 legs (slots 0..1)
@@ -752,11 +753,13 @@ int npb::enqueue_energy(npb_grid *g, const npb_opts *o, cudaStream_t st) {
         for (int s = 0; s < n; ++s)
             if ((rc = run_step(g, prec, o->scheme, 2, 2, st))) return rc;
     }
+    }
     cudaEvent_t ev{};
     if ((rc = g->ctx->prof.begin(st, &ev))) return rc;
     void *const *U = g->d_u[prec];
     CU(launch_energy(prec, U[kLegSlot[0]], U[kLegSlot[1]], U[kLegSlot[2]], U[kLegSlot[3]],
-                     g->d_ent_off, g->d_ent_qt, g->sc.total, re, g->d_result, st));
+                     g->d_ent_off, g->d_ent_qt, g->sc.total, re, o->vacuum_recovery ? nullptr : g->d_vac_fft,
+                     g->d_result, st));
     if ((rc = g->ctx->prof.end(st, ev, K_ENERGY))) return rc;
     CU(cudaMemcpyAsync(g->h_result, g->d_result, sizeof(double), cudaMemcpyDeviceToHost, st));
     CU(cudaMemcpyAsync(reinterpret_cast<int32_t *>(g->h_result + 1), g->d_err, sizeof(int32_t),
@@ -768,7 +771,7 @@ int npb::enqueue_energy(npb_grid *g, const npb_opts *o, cudaStream_t st) {
 int npb::enqueue_energy_reduce(npb_grid *g, int prec, int richardson, cudaStream_t st) {
     void *const *U = g->d_u[prec];
     CU(launch_energy(prec, U[kLegSlot[0]], U[kLegSlot[1]], U[kLegSlot[2]], U[kLegSlot[3]], g->d_ent_off,
-                     g->d_ent_qt, g->sc.total, richardson, g->d_result, st));
+                     g->d_ent_qt, g->sc.total, richardson, nullptr, g->d_result, st));
     CU(cudaMemcpyAsync(g->h_result, g->d_result, sizeof(double), cudaMemcpyDeviceToHost, st));
     CU(cudaMemcpyAsync(reinterpret_cast<int32_t *>(g->h_result + 1), g->d_err, sizeof(int32_t),
                        cudaMemcpyDeviceToHost, st));
@@ -796,23 +799,24 @@ extern "C" int npb_energy(npb_grid *g, const npb_opts *o, double *dG) {
     if (!g || !dG) return fail(NPB_EINVAL, "grid/dG is NULL");
     int rc = check_opts(o);
     if (rc) return rc;
-    if (!o->vacuum_recovery)
-        return fail(NPB_EINVAL, "vacuum_recovery = 0 needs the FFT vacuum potential, which is not provided");
     npb_ctx *ctx = g->ctx;
     CU(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
     if ((rc = grid_prepare(g, o, st))) return rc;
-    // boundary data are computed on first use, outside any graph capture
+    // boundary data (and phi_0^FFT) are computed on first use, outside any graph capture
     const int legs[4] = {0, 1, 2, 3};
     for (int i = 0; i < 4; ++i) {
         const double *bc;
         if ((rc = grid_boundary(g, legs[i] < 2 ? NPB_SOLVENT : NPB_VACUUM, o->precision, st, &bc))) return rc;
     }
+    if (!o->vacuum_recovery && (rc = grid_vacuum_fft(g, o->precision, st))) return rc;
+    g->last_richardson = o->richardson ? 1 : 0;
+    g->last_vacuum_lod = o->vacuum_recovery ? 1 : 0;
     const bool use_graph = !ctx->prof.enabled && st != nullptr && ctx->use_graphs;
     if (use_graph) {
         char key[256];
-        snprintf(key, sizeof key, "%d/%d/%d/%d/%d/%s", o->precision, o->scheme, o->richardson, o->n_steps,
-                 o->eps_mode, g->legs_key[o->precision].c_str());
+        snprintf(key, sizeof key, "%d/%d/%d/%d/%d/%d/%s", o->precision, o->scheme, o->richardson, o->n_steps,
+                 o->eps_mode, o->vacuum_recovery, g->legs_key[o->precision].c_str());
         GraphCache *hit = nullptr;
         for (auto &c : g->graphs)
             if (c.key == key && c.stream == st) hit = &c;
@@ -866,16 +870,27 @@ extern "C" int npb_lod_solve(npb_grid *g, const npb_opts *o, int32_t medium, dou
 
 extern "C" int npb_potential(npb_grid *g, int32_t leg, double *host_out, size_t n_elems) {
     if (!g || !host_out) return fail(NPB_EINVAL, "grid/host_out is NULL");
-    if (leg < 0 || leg > 3) return fail(NPB_EINVAL, "unknown leg %d", leg);
+    if (leg < 0 || leg > NPB_LEG_RECOVERED) return fail(NPB_EINVAL, "unknown leg %d", leg);
     const size_t total = (size_t)g->geo.nx * g->geo.ny * g->geo.nz;
     if (n_elems != total) return fail(NPB_EINVAL, "n_elems %zu != nx*ny*nz %zu", n_elems, total);
     if (g->u_prec < 0 || !g->d_u[g->u_prec][0]) return fail(NPB_EINVAL, "no solve has run on this grid");
+    if (leg == NPB_LEG_RECOVERED && !g->last_vacuum_lod)
+        return fail(NPB_EINVAL, "the recovered potential needs a solve with the LOD vacuum legs");
     CU(cudaSetDevice(g->ctx->device));
     cudaStream_t st = g->ctx->stream;
+    int rc;
+    if (leg >= NPB_LEG_VACUUM_FFT && (rc = grid_vacuum_fft(g, g->u_prec, st))) return rc;
     void *tmp = nullptr;
-    int rc = g->ctx->alloc(&tmp, total * sizeof(double));
-    if (rc) return rc;
-    cudaError_t e = unpad_state(g->u_prec, g->geo, g->d_u[g->u_prec][kLegSlot[leg]], (double *)tmp, st);
+    if ((rc = g->ctx->alloc(&tmp, total * sizeof(double)))) return rc;
+    void *const *U = g->d_u[g->u_prec];
+    cudaError_t e;
+    if (leg == NPB_LEG_VACUUM_FFT)
+        e = unpad_state(NPB_FP64, g->geo, g->d_vac_fft, (double *)tmp, st);
+    else if (leg == NPB_LEG_RECOVERED)
+        e = launch_recover(g->u_prec, g->geo, U[kLegSlot[0]], U[kLegSlot[1]], U[kLegSlot[2]], U[kLegSlot[3]],
+                           g->d_vac_fft, g->last_richardson, (double *)tmp, st);
+    else
+        e = unpad_state(g->u_prec, g->geo, U[kLegSlot[leg]], (double *)tmp, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, tmp, total * sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     g->ctx->release(tmp, total * sizeof(double));

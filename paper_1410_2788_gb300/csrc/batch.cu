@@ -211,7 +211,7 @@ extern "C" int npb_energy_batch(npb_grid *const *grids, int32_t n_grids, const n
     if (o->precision != NPB_FP64 && o->precision != NPB_FP32_SWEEP)
         return fail(NPB_EINVAL, "unknown precision %d", o->precision);
     if (!o->vacuum_recovery)
-        return fail(NPB_EINVAL, "vacuum_recovery = 0 needs the FFT vacuum potential, which is not provided");
+        return fail(NPB_EINVAL, "npb_energy_batch runs the LOD vacuum legs (vacuum_recovery = 1); use npb_energy");
     npb_ctx *ctx = grids[0] ? grids[0]->ctx : nullptr;
     for (int i = 0; i < n_grids; ++i) {
         if (!grids[i]) return fail(NPB_EINVAL, "grids[%d] is NULL", i);

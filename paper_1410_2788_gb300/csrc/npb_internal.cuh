@@ -79,6 +79,9 @@ cudaError_t launch_nonlinear(int prec, const LegDev *legs_dev, int n_legs, int n
 cudaError_t launch_source(int prec, const LegDev *legs_dev, int n_legs, int ny, int nz,
                           cudaStream_t st);
 struct GridGeom;
+// phi_m^LOD + phi_0^LOD - phi_0^FFT as dense FP64 (the recovered potential of Sec. 5.3).
+cudaError_t launch_recover(int prec, const GridGeom &g, const void *s_tau, const void *s_half, const void *v_tau,
+                           const void *v_half, const double *vac, int richardson, double *out, cudaStream_t st);
 // u += src at the interior nodes of a padded state (dense source stage).
 cudaError_t launch_add_interior(int prec, const GridGeom &g, const void *src, void *u, cudaStream_t st);
 

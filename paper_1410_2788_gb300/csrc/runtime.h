@@ -119,6 +119,11 @@ struct npb_grid {
     npb::LegDev *d_legs[2] = {};       // device leg tables by precision
     npb::LegDev h_legs[2][4];
     std::string legs_key[2];
+    double *d_vac_fft = nullptr;  // phi_0^FFT of Eq. (deltaG2), padded FP64 (fft_vacuum.cu)
+    bool vac_fft_valid = false;
+    int vac_fft_kind = -1;         // face flavour it was built from (0 FP64 pairs, 1 FP32 pairs)
+    int last_richardson = 1;       // flags of the last npb_energy (for the recovered potential)
+    int last_vacuum_lod = 1;
     double *d_result = nullptr;
     double *h_result = nullptr;  // pinned
     int32_t *d_err = nullptr;    // set by a device wait that expired
@@ -136,6 +141,23 @@ struct npb_grid {
 
 namespace npb {
 using Grid = ::npb_grid;
+
+// Bytes of one padded state of n nodes (x-rows padded to 32 elements).
+inline size_t state_bytes(const int n[3], int prec) {
+    const size_t pitch = (size_t)(n[0] + 31) / 32 * 32;
+    return pitch * n[1] * n[2] * (prec == NPB_FP64 ? 8 : 4);
+}
+
+// count elements of T on the device, owned by the grid (freed with it).
+template <typename T>
+int galloc(Grid *g, T **p, size_t count) {
+    void *v = nullptr;
+    int rc = g->ctx->alloc(&v, count * sizeof(T));
+    if (rc) return rc;
+    g->allocs.push_back({v, count * sizeof(T)});
+    *p = static_cast<T *>(v);
+    return 0;
+}
 
 extern const int kLegSlot[4];
 
@@ -162,6 +184,7 @@ int init_legs(Grid *g, int prec, const int *legs, int n, cudaStream_t st);
 int enqueue_energy(Grid *g, const npb_opts *o, cudaStream_t st);
 void serve_shutdown(Ctx *ctx);
 void batch_forget(Ctx *ctx, Grid *g);  // drop batch plans naming g (all plans when g is null)
+int grid_vacuum_fft(Grid *g, int prec, cudaStream_t st);  // phi_0^FFT into g->d_vac_fft
 
 }  // namespace npb
 

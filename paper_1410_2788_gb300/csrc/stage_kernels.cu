@@ -95,7 +95,8 @@ template <typename T>
 __global__ void k_energy(const T *__restrict__ s_tau, const T *__restrict__ s_half,
                          const T *__restrict__ v_tau, const T *__restrict__ v_half,
                          const int64_t *__restrict__ off, const double *__restrict__ qt,
-                         const int32_t *__restrict__ n_ent_dev, int richardson, double *__restrict__ out) {
+                         const int32_t *__restrict__ n_ent_dev, int richardson, const double *__restrict__ vac,
+                         double *__restrict__ out) {
     __shared__ double part[1024];
     const int n_ent = *n_ent_dev;
     double acc = 0.0;
@@ -104,11 +105,12 @@ __global__ void k_energy(const T *__restrict__ s_tau, const T *__restrict__ s_ha
         double us, uv;
         if (richardson) {
             us = 2.0 * (double)s_half[p] - (double)s_tau[p];
-            uv = 2.0 * (double)v_half[p] - (double)v_tau[p];
+            uv = vac ? 0.0 : 2.0 * (double)v_half[p] - (double)v_tau[p];
         } else {
             us = (double)s_tau[p];
-            uv = (double)v_tau[p];
+            uv = vac ? 0.0 : (double)v_tau[p];
         }
+        if (vac) uv = vac[p];  // Eq. (deltaG2): phi_0^FFT in place of the vacuum legs
         acc += qt[e] * (us - uv);
     }
     part[threadIdx.x] = acc;
@@ -122,15 +124,46 @@ __global__ void k_energy(const T *__restrict__ s_tau, const T *__restrict__ s_ha
 
 cudaError_t launch_energy(int prec, const void *s_tau, const void *s_half, const void *v_tau,
                           const void *v_half, const int64_t *off, const double *qt, const int32_t *n_ent,
-                          int richardson, double *out, cudaStream_t st) {
+                          int richardson, const double *vac, double *out, cudaStream_t st) {
     if (prec == 0)
         k_energy<double><<<1, 1024, 0, st>>>((const double *)s_tau, (const double *)s_half,
                                              (const double *)v_tau, (const double *)v_half, off, qt,
-                                             n_ent, richardson, out);
+                                             n_ent, richardson, vac, out);
     else
         k_energy<float><<<1, 1024, 0, st>>>((const float *)s_tau, (const float *)s_half,
                                             (const float *)v_tau, (const float *)v_half, off, qt, n_ent,
-                                            richardson, out);
+                                            richardson, vac, out);
+    return cudaGetLastError();
+}
+
+// The recovered potential phi_m^LOD + phi_0^LOD - phi_0^FFT (Sec. 5.3), each LOD potential
+// Richardson-combined when `richardson`, as dense FP64 (x fastest).
+template <typename T>
+__global__ void k_recover(GridGeom g, const T *__restrict__ s_tau, const T *__restrict__ s_half,
+                          const T *__restrict__ v_tau, const T *__restrict__ v_half, const double *__restrict__ vac,
+                          int richardson, double *__restrict__ out) {
+    const int64_t total = (int64_t)g.nx * g.ny * g.nz;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(q % g.nx);
+        const int64_t r = q / g.nx;
+        const int64_t p = r * g.pitch + i;
+        const double us = richardson ? 2.0 * (double)s_half[p] - (double)s_tau[p] : (double)s_tau[p];
+        const double uv = richardson ? 2.0 * (double)v_half[p] - (double)v_tau[p] : (double)v_tau[p];
+        out[q] = us + uv - vac[p];
+    }
+}
+
+cudaError_t launch_recover(int prec, const GridGeom &g, const void *s_tau, const void *s_half, const void *v_tau,
+                           const void *v_half, const double *vac, int richardson, double *out, cudaStream_t st) {
+    const int64_t total = (int64_t)g.nx * g.ny * g.nz;
+    const int b = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    if (prec == 0)
+        k_recover<double><<<b, 256, 0, st>>>(g, (const double *)s_tau, (const double *)s_half, (const double *)v_tau,
+                                             (const double *)v_half, vac, richardson, out);
+    else
+        k_recover<float><<<b, 256, 0, st>>>(g, (const float *)s_tau, (const float *)s_half, (const float *)v_tau,
+                                            (const float *)v_half, vac, richardson, out);
     return cudaGetLastError();
 }
 

@@ -290,11 +290,13 @@ def test_invalid_arguments(npb, ctx):
     assert e.value.code == npb.NPB_EINVAL
     g = npb.npb_grid_create(ctx, p)
     try:
-        for o in [npb.make_opts(-0.1, 1.0, 5), npb.make_opts(0.1, 0.0, 5), npb.make_opts(0.1, 1.0, 5, scheme=7),
-                  npb.make_opts(0.1, 1.0, 5, vacuum_recovery=False)]:
+        for o in [npb.make_opts(-0.1, 1.0, 5), npb.make_opts(0.1, 0.0, 5), npb.make_opts(0.1, 1.0, 5, scheme=7)]:
             with pytest.raises(npb.NpbError) as e:
                 npb.npb_energy(g, o)
             assert e.value.code == npb.NPB_EINVAL
+        with pytest.raises(npb.NpbError) as e:  # the batched path runs the LOD vacuum legs only
+            npb.npb_energy_batch([g], npb.make_opts(0.1, 1.0, 5, vacuum_recovery=False))
+        assert e.value.code == npb.NPB_EINVAL
         with pytest.raises(npb.NpbError):
             npb.npb_lod_solve(g, npb.make_opts(0.1, 1.0, 5), 0, 0.3)
     finally:
