@@ -23,6 +23,7 @@ import hashlib
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -219,8 +220,34 @@ def cpu_baseline(problem, w, budget_s: float = 12.0):
         if el > budget_s / 2 or reps >= 3:
             break
     value = point_steps(problem, n_s) * reps / el / 1e6
-    return {"value": value, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
-            "sample": f"{reps} RE+V solve(s) of the same molecule with {n_s} steps per dt leg"}
+    # one thread on a smaller sample (a single RE+V solve with fewer steps)
+    cores = oracle.get_threads()
+    oracle.set_threads(1)
+    n_1 = max(1, n_s // 8)
+    t1 = time.perf_counter()
+    oracle.energy(problem, w["dt"] / w["alpha"], n_1)
+    single = point_steps(problem, n_1) / (time.perf_counter() - t1) / 1e6
+    oracle.set_threads(cores)
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{reps} RE+V solve(s) of the same molecule with {n_s} steps per dt leg",
+            "single_thread": {"value": single, "unit": UNIT,
+                              "sample": f"1 RE+V solve with {n_1} steps per dt leg"},
+            "cpu_model": cpu_model()}
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (Linux /proc/cpuinfo; Arm boards report implementer/part)."""
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+    except OSError:
+        return platform.processor() or platform.machine()
+    for key in ("model name", "Model", "Hardware"):
+        for line in info:
+            if line.split(":")[0].strip() == key:
+                return line.split(":", 1)[1].strip()
+    imp = [l.split(":", 1)[1].strip() for l in info if l.startswith("CPU implementer")]
+    part = [l.split(":", 1)[1].strip() for l in info if l.startswith("CPU part")]
+    return f"{platform.machine()} implementer {imp[0] if imp else '?'} part {part[0] if part else '?'}"
 
 
 def batch_run(npb, count: int, reps: int = 3):
