@@ -43,7 +43,7 @@ KT_KCAL = 0.592183
 C_BJERRUM = COULOMB_KCAL_A / KT_KCAL  # e_c^2/(k_B T) in A at 298 K
 
 SOLVENT, VACUUM = 0, 1
-LODIE1, LODIE2 = 1, 2
+LODIE1, LODIE2, LODCN1, LODCN2 = 1, 2, 3, 4
 
 
 def build(force: bool = False) -> str:
@@ -76,6 +76,7 @@ def _load():
     lib.or_boundary.argtypes = [i, i, i, d, dp, i, dp, dp, d, d, d, dp]
     lib.or_eps_half_harmonic.argtypes = [i, i, i, dp, dp, dp, dp]
     lib.or_sweep.argtypes = [i, i, i, dp, dp, i, d]
+    lib.or_sweep_cn.argtypes = [i, i, i, dp, dp, i, d]
     lib.or_ana3.argtypes = [d, d]
     lib.or_ana3.restype = d
     lib.or_nonlinear.argtypes = [i, i, i, dp, dp, d]
@@ -216,6 +217,12 @@ def setup(problem, medium: int, eps_mode: str = "harmonic") -> Setup:
 def sweep(u: np.ndarray, e_half: np.ndarray, direction: int, tau: float, h: float) -> None:
     nz, ny, nx = u.shape
     _load().or_sweep(nx, ny, nz, _p(u), _p(e_half), direction, tau / (h * h))
+
+
+def sweep_cn(u: np.ndarray, e_half: np.ndarray, direction: int, tau: float, h: float) -> None:
+    """Eqs. (LODCN1_2)-(LODCN1_4): the Crank-Nicolson sweep along `direction`."""
+    nz, ny, nx = u.shape
+    _load().or_sweep_cn(nx, ny, nz, _p(u), _p(e_half), direction, tau / (h * h))
 
 
 def nonlinear(u: np.ndarray, kappa2_node: np.ndarray, tau: float) -> None:

@@ -16,9 +16,11 @@
  *   or_eps_half_*        eps at half points used by Eq. (SpatialOperators)
  *   or_sweep             Eqs. (LODIE1_2)-(LODIE1_4): (1 - dt/alpha delta^2) v = w,
  *                        one tridiagonal system per grid line, Thomas algorithm
+ *   or_sweep_cn          Eqs. (LODCN1_2)-(LODCN1_4): (1 - dt/(2 alpha) delta^2) v =
+ *                        (1 + dt/(2 alpha) delta^2) w, the same solve on the explicit half step
  *   or_nonlinear         Eq. (ana3), the analytic solution of alpha w_t = -kbar^2 sinh w
  *   or_source            Eq. (LODIE1_5), u += dt/alpha * Q
- *   or_lod_run           LODIE1 (N,X,Y,Z,S) or LODIE2 (S,X,Y,Z,N) steps (Sec. 3.1)
+ *   or_lod_run           LODIE1 (N,X,Y,Z,S), LODIE2 (S,X,Y,Z,N), LODCN1, LODCN2 steps (Sec. 3.1)
  *   or_euler_run         explicit Euler steps of Eq. (TimeDepNPB) (Sec. 5.2 reference)
  *
  * Layout: node (i,j,k) of an nx*ny*nz grid is stored at u[(k*ny + j)*nx + i];
@@ -207,6 +209,42 @@ void or_sweep(int nx, int ny, int nz, double *u, const double *e_half, int dir, 
     }
 }
 
+/* Eqs. (LODCN1_2)-(LODCN1_4): per line, the right-hand side is the explicit half step
+ * w + (r/2) [e_{+1/2} (w_{t+1} - w_t) - e_{-1/2} (w_t - w_{t-1})] of the line's values (faces
+ * included), then the implicit half step is the or_sweep solve with r/2. */
+void or_sweep_cn(int nx, int ny, int nz, double *u, const double *e_half, int dir, double r) {
+    const int n[3] = {nx, ny, nz};
+    const int64_t stride[3] = {1, nx, (int64_t)nx * ny};
+    const int len = n[dir];
+    const int o1 = dir == 0 ? 1 : 0, o2 = dir == 2 ? 1 : 2;
+    const int m = len - 2;
+    if (m <= 0) return;
+    const int64_t s = stride[dir];
+    const int n1 = n[o1], n2 = n[o2];
+    const double hr = 0.5 * r; /* r/2: each half step */
+#pragma omp parallel num_threads(g_threads)
+    {
+        double *w = (double *)malloc(sizeof(double) * (size_t)len);
+#pragma omp for collapse(2) schedule(static)
+        for (int b = 1; b < n2 - 1; ++b)
+            for (int a = 1; a < n1 - 1; ++a) {
+                int ijk[3];
+                ijk[dir] = 0;
+                ijk[o1] = a;
+                ijk[o2] = b;
+                const int64_t base = idx3(ijk[0], ijk[1], ijk[2], nx, ny);
+                for (int t = 0; t < len; ++t) w[t] = u[base + (int64_t)t * s];
+                for (int t = 1; t < len - 1; ++t) {
+                    const int64_t p = base + (int64_t)t * s;
+                    const double em = e_half[p - s], ep = e_half[p];
+                    u[p] = w[t] + hr * (ep * (w[t + 1] - w[t]) - em * (w[t] - w[t - 1]));
+                }
+            }
+        free(w);
+    }
+    or_sweep(nx, ny, nz, u, e_half, dir, hr);
+}
+
 /* Eq. (ana3) with a = kbar^2 dt / (2 alpha) = kbar^2 tau / 2:
  *   W' = ln[(cosh a + e^{-W} sinh a) / (e^{-W} cosh a + sinh a)].
  * The map is odd in W, so it is evaluated at |W|, where e^{-|W|} <= 1 cannot overflow.
@@ -243,18 +281,27 @@ void or_source(int nx, int ny, int nz, double *u, const double *rho, double tau)
 
 /* n_steps LOD steps with tau = dt/alpha and r = tau/h^2.
  * scheme 2 (LODIE2, Sec. 3.1): source, x, y, z, nonlinear.
- * scheme 1 (LODIE1):           nonlinear, x, y, z, source. */
+ * scheme 1 (LODIE1):           nonlinear, x, y, z, source.
+ * schemes 3, 4 (LODCN1, LODCN2): the orders of 1 and 2 with the Crank-Nicolson sweeps. */
 void or_lod_run(int nx, int ny, int nz, double *u, const double *rho, const double *kappa2_node,
                 const double *ex, const double *ey, const double *ez, double tau, double h,
                 int n_steps, int scheme) {
     const double r = tau / (h * h);
+    const int first_n = scheme == 1 || scheme == 3;
+    const int cn = scheme == 3 || scheme == 4;
     for (int s = 0; s < n_steps; ++s) {
-        if (scheme == 1) or_nonlinear(nx, ny, nz, u, kappa2_node, tau);
+        if (first_n) or_nonlinear(nx, ny, nz, u, kappa2_node, tau);
         else or_source(nx, ny, nz, u, rho, tau);
-        or_sweep(nx, ny, nz, u, ex, 0, r);
-        or_sweep(nx, ny, nz, u, ey, 1, r);
-        or_sweep(nx, ny, nz, u, ez, 2, r);
-        if (scheme == 1) or_source(nx, ny, nz, u, rho, tau);
+        if (cn) {
+            or_sweep_cn(nx, ny, nz, u, ex, 0, r);
+            or_sweep_cn(nx, ny, nz, u, ey, 1, r);
+            or_sweep_cn(nx, ny, nz, u, ez, 2, r);
+        } else {
+            or_sweep(nx, ny, nz, u, ex, 0, r);
+            or_sweep(nx, ny, nz, u, ey, 1, r);
+            or_sweep(nx, ny, nz, u, ez, 2, r);
+        }
+        if (first_n) or_source(nx, ny, nz, u, rho, tau);
         else or_nonlinear(nx, ny, nz, u, kappa2_node, tau);
     }
 }

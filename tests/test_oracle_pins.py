@@ -415,3 +415,53 @@ def test_vacuum_lod_leg_tends_to_fft(oracle_lib):
         u = oracle_lib.lod_leg(p, oracle_lib.VACUUM, tau, int(round(40.0 / tau)))
         d.append(np.max(np.abs(u - ref)) / np.max(np.abs(ref)))
     assert d[2] < 0.05 and all(1.6 < a / b < 2.4 for a, b in zip(d, d[1:])), d
+
+
+# --------------------------------------------------------------------------- LODCN (Sec. 3.1)
+@pytest.mark.parametrize("h", [0.5, 0.25])
+def test_paper_table2_lodcn_sphere_errors(oracle_lib, h):
+    """Table 2 (LODCN rows): the sphere benchmark with the Crank-Nicolson sweeps reproduces the
+    printed relative errors (midpoint eps, as for the LODIE rows)."""
+    rows = {float(r[0]): (float(r[1]), float(r[2])) for r in _golden("paper_table2_lodcn.txt")}
+    (l2, linf), _ = sphere_case.run(h, scheme=4)
+    ref_l2, ref_linf = rows[h]
+    assert abs(l2 - ref_l2) <= 0.006 * ref_l2, (h, l2, ref_l2)
+    assert abs(linf - ref_linf) <= 0.006 * ref_linf, (h, linf, ref_linf)
+
+
+def test_paper_lodcn1_equals_lodcn2_on_sphere(oracle_lib):
+    """Sec. 4.3: LODCN1 and LODCN2 print the same errors on the sphere."""
+    (a2, ai), _ = sphere_case.run(0.5, scheme=3)
+    (b2, bi), _ = sphere_case.run(0.5, scheme=4)
+    assert f"{a2:.2e}" == f"{b2:.2e}" and f"{ai:.2e}" == f"{bi:.2e}"
+
+
+def test_cn_sweep_equals_dense_solve(oracle_lib):
+    """One Crank-Nicolson x sweep = the dense solve of (I - r/2 A) v = (I + r/2 A) w per line,
+    A the eps-weighted 3-point operator with the face values as Dirichlet data."""
+    rng = np.random.default_rng(5)
+    nz, ny, nx = 4, 5, 9
+    tau, h = 0.7, 0.5
+    u = rng.normal(size=(nz, ny, nx))
+    eps_node = rng.uniform(1.0, 80.0, size=(nz, ny, nx))
+    ex, ey, ez = oracle_lib.eps_half_harmonic(eps_node)
+    got = u.copy()
+    oracle_lib.sweep_cn(got, ex, 0, tau, h)
+    r = tau / h ** 2
+    ref = u.copy()
+    for k in range(1, nz - 1):
+        for j in range(1, ny - 1):
+            w = u[k, j, :]
+            e = ex[k, j, :]  # e[i] = eps at i + 1/2
+            m = nx - 2
+            A = np.zeros((m, nx))
+            for t in range(1, nx - 1):
+                A[t - 1, t - 1] += e[t - 1]
+                A[t - 1, t] -= e[t - 1] + e[t]
+                A[t - 1, t + 1] += e[t]
+            rhs = w[1:-1] + 0.5 * r * (A @ w)
+            M = -0.5 * r * A
+            M[:, 1:-1] += np.eye(m)
+            rhs2 = rhs - M[:, 0] * w[0] - M[:, -1] * w[-1]
+            ref[k, j, 1:-1] = np.linalg.solve(M[:, 1:-1], rhs2)
+    assert np.allclose(got, ref, rtol=1e-12, atol=1e-12)
