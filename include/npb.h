@@ -55,6 +55,8 @@ extern "C" {
 
 #define NPB_LODIE2 2        /* S, X, Y, Z, N  (Sec. 3.1; the paper's chosen scheme)     */
 #define NPB_LODIE1 1        /* N, X, Y, Z, S                                            */
+#define NPB_LODCN1 3        /* LODIE1's order with the Crank-Nicolson sweeps (Eqs. LODCN1_2-4) */
+#define NPB_LODCN2 4        /* LODIE2's order with the Crank-Nicolson sweeps            */
 
 #define NPB_FP64 0          /* every stage in FP64                                      */
 #define NPB_FP32_SWEEP 1    /* potential stored and swept in FP32; energy in FP64       */
@@ -116,7 +118,7 @@ typedef struct {
 typedef struct {
     double dt, alpha;
     int32_t n_steps;
-    int32_t scheme;           /* NPB_LODIE2 (default) or NPB_LODIE1                   */
+    int32_t scheme;           /* NPB_LODIE2 (default), NPB_LODIE1, NPB_LODCN1/2       */
     int32_t richardson;       /* 1: RE of Eq. (rich)                                   */
     int32_t vacuum_recovery;  /* 1: LOD vacuum legs of Eq. (deltaG3); 0: Eq. (deltaG2) */
     int32_t precision;        /* NPB_FP64 or NPB_FP32_SWEEP                            */

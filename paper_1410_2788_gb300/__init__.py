@@ -25,7 +25,7 @@ LIB_PATH = os.path.join(_HERE, "libnpb.so")
 NPB_OK, NPB_PENDING = 0, 1
 NPB_EINVAL, NPB_ENOMEM, NPB_ECUDA, NPB_ETIMEOUT, NPB_ENOTFOUND, NPB_ESHUTDOWN = -1, -2, -3, -4, -5, -6
 NPB_SOLVENT, NPB_VACUUM = 0, 1
-NPB_LODIE1, NPB_LODIE2 = 1, 2
+NPB_LODIE1, NPB_LODIE2, NPB_LODCN1, NPB_LODCN2 = 1, 2, 3, 4
 NPB_FP64, NPB_FP32_SWEEP = 0, 1
 NPB_EPS_HARMONIC, NPB_EPS_MIDPOINT = 0, 1
 NPB_LEG_SOLVENT_TAU, NPB_LEG_SOLVENT_HALF, NPB_LEG_VACUUM_TAU, NPB_LEG_VACUUM_HALF = 0, 1, 2, 3

@@ -87,7 +87,7 @@ cudaError_t launch_sweep(int prec, int dir, const LegDev *legs, int n_legs, int 
 }
 
 const char *kKernelNames[K_COUNT] = {"sweep_x", "sweep_y", "sweep_z", "nonlinear", "source", "init_leg",
-                                     "energy", "setup_mask", "setup_charges", "setup_boundary", "pad"};
+                                     "energy", "setup_mask", "setup_charges", "setup_boundary", "pad", "cn_explicit"};
 }  // namespace npb
 
 // ------------------------------------------------------------------ context
@@ -495,7 +495,8 @@ LegDev npb::make_leg(const npb_grid *g, int leg, const npb_opts *o) {
     const bool half = leg == NPB_LEG_SOLVENT_HALF || leg == NPB_LEG_VACUUM_HALF;
     const double tau = (half ? 0.5 : 1.0) * o->dt / o->alpha;
     const double h = g->geo.h;
-    const double r = tau / (h * h);
+    // the Crank-Nicolson sweeps split r between their explicit and implicit halves (Eq. LODCN1_2)
+    const double r = tau / (h * h) * (o->scheme >= NPB_LODCN1 ? 0.5 : 1.0);
     L.u = g->d_u[prec][kLegSlot[leg]];
     L.nx = g->geo.nx;
     L.ny = g->geo.ny;
@@ -537,7 +538,7 @@ static int check_opts(const npb_opts *o) {
     if (!o) return fail(NPB_EINVAL, "opts is NULL");
     if (!(o->dt > 0) || !(o->alpha > 0)) return fail(NPB_EINVAL, "dt and alpha must be > 0");
     if (o->n_steps < 0) return fail(NPB_EINVAL, "n_steps < 0");
-    if (o->scheme != NPB_LODIE1 && o->scheme != NPB_LODIE2) return fail(NPB_EINVAL, "unknown scheme %d", o->scheme);
+    if (o->scheme < NPB_LODIE1 || o->scheme > NPB_LODCN2) return fail(NPB_EINVAL, "unknown scheme %d", o->scheme);
     if (o->precision != NPB_FP64 && o->precision != NPB_FP32_SWEEP)
         return fail(NPB_EINVAL, "unknown precision %d", o->precision);
     if (o->eps_mode != NPB_EPS_HARMONIC && o->eps_mode != NPB_EPS_MIDPOINT)
@@ -554,7 +555,7 @@ int npb::grid_prepare(npb_grid *g, const npb_opts *o, cudaStream_t st) {
     const int prec = o->precision;
     g->u_prec = prec;
     char key[256];
-    snprintf(key, sizeof key, "%.17g/%.17g/%d", o->dt, o->alpha, o->eps_mode);
+    snprintf(key, sizeof key, "%.17g/%.17g/%d/%d", o->dt, o->alpha, o->eps_mode, o->scheme >= NPB_LODCN1 ? 1 : 0);
     if (g->legs_key[prec] == key) return 0;
     for (int leg = 0; leg < 4; ++leg) g->h_legs[prec][kLegSlot[leg]] = make_leg(g, leg, o);
     CU(cudaMemcpyAsync(g->d_legs[prec], g->h_legs[prec], sizeof(LegDev) * 4, cudaMemcpyHostToDevice, st));
@@ -656,17 +657,31 @@ int npb::step_legs(npb_ctx *ctx, const LegRef *refs, int n, const LegDev *d_tabl
     }
     cudaEvent_t ev{};
     int rc;
+    // Crank-Nicolson schemes: the first stage runs on its own (the explicit half step of x must see
+    // its result), then each direction is the explicit half step followed by the implicit sweep
+    const bool cn = scheme >= NPB_LODCN1;
+    const bool first_n = scheme == NPB_LODIE1 || scheme == NPB_LODCN1;
     // LODIE2's source stage: fused into the x sweep's load except by the kind-1 TMA kernel
-    const bool src_apart = scheme == NPB_LODIE2 && tma[0] && shape[0].kind == 1;
+    const bool src_apart = !first_n && (cn || (tma[0] && shape[0].kind == 1));
     if (src_apart) {
         if ((rc = pr.begin(st, &ev))) return rc;
         CU(launch_source(prec, d_table, n, ny, nz, st));
         if ((rc = pr.end(st, ev, K_SOURCE))) return rc;
     }
+    if (cn && first_n) {
+        if ((rc = pr.begin(st, &ev))) return rc;
+        CU(launch_nonlinear(prec, d_table, n, nx, ny, nz, st));
+        if ((rc = pr.end(st, ev, K_NONLINEAR))) return rc;
+    }
     for (int d = 0; d < 3; ++d) {
         int flags = 0;
-        if (d == 0) flags = scheme == NPB_LODIE2 ? (src_apart ? 0 : FUSE_PRE_SRC) : FUSE_PRE_NL;
-        if (d == 2 && scheme == NPB_LODIE2) flags = FUSE_POST_NL;
+        if (d == 0 && !cn) flags = !first_n ? (src_apart ? 0 : FUSE_PRE_SRC) : FUSE_PRE_NL;
+        if (d == 2 && !first_n) flags = FUSE_POST_NL;
+        if (cn) {
+            if ((rc = pr.begin(st, &ev))) return rc;
+            CU(launch_cn_explicit(prec, d_table, n, d, st));
+            if ((rc = pr.end(st, ev, K_CN_EXPLICIT))) return rc;
+        }
         if ((rc = pr.begin(st, &ev))) return rc;
         if (tma[d]) {
             const int v = tma_variant(d, shape[d].tx);
@@ -690,7 +705,7 @@ int npb::step_legs(npb_ctx *ctx, const LegRef *refs, int n, const LegDev *d_tabl
         }
         if ((rc = pr.end(st, ev, K_SWEEP_X + d))) return rc;
     }
-    if (scheme == NPB_LODIE1) {
+    if (first_n) {
         if ((rc = pr.begin(st, &ev))) return rc;
         CU(launch_source(prec, d_table, n, ny, nz, st));
         if ((rc = pr.end(st, ev, K_SOURCE))) return rc;
@@ -1002,15 +1017,21 @@ extern "C" int npb_lod_run(npb_grid *g, const npb_opts *o, int32_t leg, int32_t 
             if ((rc = run_step(g, prec, o->scheme, slot, 1, st))) return done(rc);
             continue;
         }
-        // the stages of Sec. 3.1 with S = u + tau rho: LODIE2 S, X, Y, Z, N; LODIE1 N, X, Y, Z, S
-        if (o->scheme == NPB_LODIE2 && (e = launch_add_interior(prec, g->geo, src, u, st)) != cudaSuccess) break;
+        // the stages of Sec. 3.1 with S = u + tau rho: LODIE2/LODCN2 S, X, Y, Z, N;
+        // LODIE1/LODCN1 N, X, Y, Z, S (Crank-Nicolson: each sweep after its explicit half step)
+        const bool cn = o->scheme >= NPB_LODCN1;
+        const bool first_n = o->scheme == NPB_LODIE1 || o->scheme == NPB_LODCN1;
+        const LegDev *legs = g->d_legs[prec] + slot;
+        if (!first_n) e = launch_add_interior(prec, g->geo, src, u, st);
+        else if (cn) e = launch_nonlinear(prec, legs, 1, n_dir[0], n_dir[1], n_dir[2], st);
         for (int d = 0; d < 3 && e == cudaSuccess; ++d) {
             int flags = 0;
-            if (d == 0 && o->scheme == NPB_LODIE1) flags = FUSE_PRE_NL;
-            if (d == 2 && o->scheme == NPB_LODIE2) flags = FUSE_POST_NL;
-            e = launch_dir(g, prec, d, shape_for(g->ctx, prec, d, n_dir[d]), slot, 1, flags, st);
+            if (d == 0 && first_n && !cn) flags = FUSE_PRE_NL;
+            if (d == 2 && !first_n) flags = FUSE_POST_NL;
+            if (cn) e = launch_cn_explicit(prec, legs, 1, d, st);
+            if (e == cudaSuccess) e = launch_dir(g, prec, d, shape_for(g->ctx, prec, d, n_dir[d]), slot, 1, flags, st);
         }
-        if (e == cudaSuccess && o->scheme == NPB_LODIE1) e = launch_add_interior(prec, g->geo, src, u, st);
+        if (e == cudaSuccess && first_n) e = launch_add_interior(prec, g->geo, src, u, st);
         if (e != cudaSuccess) break;
     }
     if (e == cudaSuccess) e = unpad_state(prec, g->geo, u, (double *)tmp, st);

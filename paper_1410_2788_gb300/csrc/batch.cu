@@ -87,7 +87,7 @@ static int plan_build(Ctx *ctx, Grid *const *grids, int n, const npb_opts *o, Ba
     for (auto &q : plan->groups) {
         const Grid *g0 = q.grids[0];
         const int dims[3] = {g0->geo.nx, g0->geo.ny, g0->geo.nz};
-        bool ok = prec == NPB_FP32_SWEEP && o->eps_mode == NPB_EPS_HARMONIC;
+        bool ok = prec == NPB_FP32_SWEEP && o->eps_mode == NPB_EPS_HARMONIC && o->scheme <= NPB_LODIE2;
         for (int d = 0; d < 3; ++d) {
             q.shape[d] = shape_for(ctx, prec, d, dims[d]);
             ok = ok && q.shape[d].kind == 2 && tma_variant(d, q.shape[d].tx) >= 0;
@@ -207,7 +207,7 @@ extern "C" int npb_energy_batch(npb_grid *const *grids, int32_t n_grids, const n
     if (!grids || n_grids <= 0 || !dG) return fail(NPB_EINVAL, "grids/dG is NULL or n_grids <= 0");
     if (!o) return fail(NPB_EINVAL, "opts is NULL");
     if (!(o->dt > 0) || !(o->alpha > 0) || o->n_steps < 0) return fail(NPB_EINVAL, "dt, alpha > 0, n_steps >= 0");
-    if (o->scheme != NPB_LODIE1 && o->scheme != NPB_LODIE2) return fail(NPB_EINVAL, "unknown scheme %d", o->scheme);
+    if (o->scheme < NPB_LODIE1 || o->scheme > NPB_LODCN2) return fail(NPB_EINVAL, "unknown scheme %d", o->scheme);
     if (o->precision != NPB_FP64 && o->precision != NPB_FP32_SWEEP)
         return fail(NPB_EINVAL, "unknown precision %d", o->precision);
     if (!o->vacuum_recovery)

@@ -79,6 +79,8 @@ cudaError_t launch_nonlinear(int prec, const LegDev *legs_dev, int n_legs, int n
 cudaError_t launch_source(int prec, const LegDev *legs_dev, int n_legs, int ny, int nz,
                           cudaStream_t st);
 struct GridGeom;
+// The explicit half step of the Crank-Nicolson sweeps along dir, in place, for n_legs legs.
+cudaError_t launch_cn_explicit(int prec, const LegDev *legs_dev, int n_legs, int dir, cudaStream_t st);
 // phi_m^LOD + phi_0^LOD - phi_0^FFT as dense FP64 (the recovered potential of Sec. 5.3).
 cudaError_t launch_recover(int prec, const GridGeom &g, const void *s_tau, const void *s_half, const void *v_tau,
                            const void *v_half, const double *vac, int richardson, double *out, cudaStream_t st);

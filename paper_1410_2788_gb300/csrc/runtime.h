@@ -23,7 +23,7 @@ constexpr int kMaxLine = 288;  // longest line the instantiated solver shapes co
 
 enum KernelKind {
     K_SWEEP_X = 0, K_SWEEP_Y, K_SWEEP_Z, K_NONLINEAR, K_SOURCE, K_INIT, K_ENERGY,
-    K_SETUP_MASK, K_SETUP_CHARGES, K_SETUP_BOUNDARY, K_PAD, K_COUNT
+    K_SETUP_MASK, K_SETUP_CHARGES, K_SETUP_BOUNDARY, K_PAD, K_CN_EXPLICIT, K_COUNT
 };
 extern const char *kKernelNames[K_COUNT];
 

@@ -335,7 +335,7 @@ extern "C" int npb_submit(npb_ctx *ctx, const npb_problem *p, const npb_opts *o,
     if (p->n_atoms < 0 || (p->n_atoms > 0 && (!p->xyz || !p->q || !p->radius)))
         return fail(NPB_EINVAL, "bad atom arrays");
     if (!(o->dt > 0) || !(o->alpha > 0) || o->n_steps < 0 || !o->vacuum_recovery ||
-        (o->scheme != NPB_LODIE1 && o->scheme != NPB_LODIE2) ||
+        (o->scheme < NPB_LODIE1 || o->scheme > NPB_LODCN2) ||
         (o->precision != NPB_FP64 && o->precision != NPB_FP32_SWEEP) ||
         (o->eps_mode != NPB_EPS_HARMONIC && o->eps_mode != NPB_EPS_MIDPOINT))
         return fail(NPB_EINVAL, "invalid options");

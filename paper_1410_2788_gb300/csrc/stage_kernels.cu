@@ -60,6 +60,69 @@ cudaError_t launch_nonlinear(int prec, const LegDev *legs, int n_legs, int nx, i
     return cudaGetLastError();
 }
 
+// The explicit half step of the Crank-Nicolson sweeps (Eqs. LODCN1_2-4) along `dir`, in place:
+// w_g + e_{g+1/2} (w_{g+1} - w_g) - e_{g-1/2} (w_g - w_{g-1}) at every interior node, one thread per
+// line carrying the old w_{g-1}.  e = the leg's r*eps/2 at the half point (the legs of a CN scheme
+// carry the halved values): harmonic from the two node bits, midpoint from the half-point bit.
+template <typename T>
+__global__ void k_cn_explicit(const LegDev *__restrict__ legs, int dir) {
+    const LegDev *lg = legs + blockIdx.z;
+    T *u = static_cast<T *>(lg->u);
+    const int nx = lg->nx, ny = lg->ny, nz = lg->nz, pitch = lg->pitch;
+    const int wpr = mask_words_per_row(pitch);
+    const int n[3] = {nx, ny, nz};
+    const int ndir = n[dir];
+    const int a_n = dir == 0 ? ny - 2 : nx - 2, b_n = dir == 2 ? ny - 2 : nz - 2;
+    const int64_t step = dir == 0 ? 1 : (dir == 1 ? (int64_t)pitch : (int64_t)pitch * ny);
+    const T rE0 = (T)lg->rE[0], rE1 = (T)lg->rE[1], rE2 = (T)lg->rE[2];
+    const uint32_t *mask = lg->mask;
+    const uint32_t *half = lg->eps_mode ? lg->half[dir] : nullptr;
+    const int64_t lines = (int64_t)a_n * b_n;
+    for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < lines; l += (int64_t)gridDim.x * blockDim.x) {
+        const int a = 1 + (int)(l % a_n), b = 1 + (int)(l / a_n);
+        int c[3];
+        c[dir] = 0;
+        if (dir == 0) { c[1] = a; c[2] = b; }
+        else if (dir == 1) { c[0] = a; c[2] = b; }
+        else { c[0] = a; c[1] = b; }
+        const int64_t base = ((int64_t)c[2] * ny + c[1]) * pitch + c[0];
+        auto node_in = [&](int g) -> uint32_t {  // node mask bit of node g of the line
+            if (!mask) return 1u;
+            int q[3] = {c[0], c[1], c[2]};
+            q[dir] = g;
+            return (mask[((int64_t)q[2] * ny + q[1]) * wpr + (q[0] >> 5)] >> (q[0] & 31)) & 1u;
+        };
+        auto e_half = [&](int g, uint32_t in_g, uint32_t in_g1) -> T {  // half point g + 1/2
+            if (half) {
+                int q[3] = {c[0], c[1], c[2]};
+                q[dir] = g;
+                return ((half[((int64_t)q[2] * ny + q[1]) * wpr + (q[0] >> 5)] >> (q[0] & 31)) & 1u) ? rE2 : rE0;
+            }
+            return (in_g & in_g1) ? rE2 : ((in_g | in_g1) ? rE1 : rE0);
+        };
+        T w_prev = u[base], w = u[base + step];
+        uint32_t in_prev = node_in(0), in_cur = node_in(1);
+        T em = e_half(0, in_prev, in_cur);
+        for (int g = 1; g <= ndir - 2; ++g) {
+            const T w_next = u[base + (int64_t)(g + 1) * step];
+            const uint32_t in_next = node_in(g + 1);
+            const T ep = e_half(g, in_cur, in_next);
+            u[base + (int64_t)g * step] = w + ep * (w_next - w) - em * (w - w_prev);
+            w_prev = w;
+            w = w_next;
+            in_cur = in_next;
+            em = ep;
+        }
+    }
+}
+
+cudaError_t launch_cn_explicit(int prec, const LegDev *legs, int n_legs, int dir, cudaStream_t st) {
+    dim3 grid(152 * 4, 1, n_legs);
+    if (prec == 0) k_cn_explicit<double><<<grid, 128, 0, st>>>(legs, dir);
+    else k_cn_explicit<float><<<grid, 128, 0, st>>>(legs, dir);
+    return cudaGetLastError();
+}
+
 // u += s at interior nodes, s a padded array in the state's layout (a dense source tau*rho).
 template <typename T>
 __global__ void k_add_interior(GridGeom g, const T *__restrict__ src, T *__restrict__ u) {

@@ -362,3 +362,32 @@ def test_every_solver_shape_matches_oracle(npb, O, prec):
             npb.npb_ctx_destroy(c)
         assert abs(dg - ref_dg) <= tol * abs(ref_dg), (d, kind, tx, seg, ln, dg, ref_dg)
         assert linf_rel(u, ref_legs["solvent_half"]) <= tol, (d, kind, tx, seg, ln)
+
+
+@pytest.mark.parametrize("scheme", [3, 4])
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-4)])
+def test_lodcn_step_and_energy(npb, O, scheme, precision, tol):
+    """The Crank-Nicolson schemes: one step from a random state (row-level interface) and the RE+V
+    energy against the oracle, on the ragged 37x29x23 grid."""
+    p = small_molecule()
+    c = npb.npb_ctx_create(0, 0)
+    try:
+        g = npb.npb_grid_create(c, p)
+        try:
+            st = O.setup(p, O.SOLVENT)
+            rng = np.random.default_rng(77)
+            base = st.u0 + rng.normal(0, 4.0, st.u0.shape) * (st.u0 == 0)
+            if precision == 1:
+                base = base.astype(np.float32).astype(np.float64)
+            o = npb.make_opts(0.4, 0.04, 6, scheme=scheme, precision=precision)
+            got = npb.npb_apply(g, o, 0, npb.NPB_OP_STEP, base)
+            ref = base.copy()
+            O.lod_run(ref, st, 10.0, p.h, 1, scheme)
+            assert linf_rel(got, ref) <= tol
+            dg = npb.npb_energy(g, o)
+        finally:
+            npb.npb_grid_destroy(g)
+    finally:
+        npb.npb_ctx_destroy(c)
+    ref_dg = O.energy(p, 10.0, 6, scheme=scheme)
+    assert abs(dg - ref_dg) <= tol * abs(ref_dg), (dg, ref_dg)

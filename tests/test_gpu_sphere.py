@@ -105,3 +105,29 @@ def test_sphere_table1_stable_at_dt5(npb, H, h, precision):
     """Table 1, LOD row: finite up to dt = 5 with T = 1e4 dt, H = 1 and 20, h = 0.5 and 0.25."""
     (l2, linf), u = gpu_sphere(npb, h, precision=precision, dt=5.0, n_steps=10000, H=H)
     assert np.all(np.isfinite(u)) and np.isfinite(l2) and l2 < 10.0
+
+
+def _table2_lodcn():
+    rows = {}
+    for line in open(os.path.join(HERE, "golden", "paper_table2_lodcn.txt")):
+        f = line.split()
+        if f and not line.startswith("#"):
+            rows[float(f[0])] = (float(f[1]), float(f[2]))
+    return rows
+
+
+@pytest.mark.parametrize("scheme", [4, 3])
+def test_sphere_lodcn_fp64_matches_oracle(npb, O, scheme):
+    """Crank-Nicolson LOD (LODCN2, LODCN1) on the GPU = the oracle, 1e-10 (h = 0.5)."""
+    _, u = gpu_sphere(npb, 0.5, scheme=scheme)
+    _, ref = sphere_case.run(0.5, scheme=scheme)
+    assert linf_rel(u, ref) <= 1e-10
+
+
+@pytest.mark.parametrize("h", [0.5, 0.25, 0.125, 0.0625])
+def test_sphere_reproduces_table2_lodcn(npb, h):
+    """Table 2, LODCN rows, to the printed three digits, down to h = 0.0625."""
+    (l2, linf), _ = gpu_sphere(npb, h, scheme=4)
+    ref_l2, ref_linf = _table2_lodcn()[h]
+    assert abs(l2 - ref_l2) <= 0.006 * ref_l2, (h, l2, ref_l2)
+    assert abs(linf - ref_linf) <= 0.006 * ref_linf, (h, linf, ref_linf)
