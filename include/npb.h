@@ -205,6 +205,14 @@ int npb_potential(npb_grid *grid, int32_t leg, double *host_out, size_t n_elems)
 int npb_lod_run(npb_grid *grid, const npb_opts *opts, int32_t leg, int32_t n_steps, double *u_inout,
                 const double *source, size_t n_elems);
 
+/* n_steps explicit Euler steps of Eq. (TimeDepNPB) for leg `leg` from a caller-given state
+ * (layout and faces as npb_lod_run; tau = dt/alpha, halved for the *_HALF legs; the molecule's
+ * charges as the source): u += tau (div(eps grad u) - kbar^2 sinh u + rho) with the same
+ * half-point eps as the LOD sweeps.  The conditionally stable reference the paper compares its
+ * splitting schemes with (Sec. 5.2); tau must respect h^2/(6 eps_max) for stability. */
+int npb_euler_run(npb_grid *grid, const npb_opts *opts, int32_t leg, int32_t n_steps, double *u_inout,
+                  size_t n_elems);
+
 /* Row-level access to single LOD stages: load the dense FP64 field u_inout (nz*ny*nx)
  * into leg `leg`'s state (rounded to opts->precision), apply stage `op` (NPB_OP_*)
  * with that leg's medium and tau = dt/alpha (halved for the *_HALF legs), and copy the

@@ -83,6 +83,7 @@ SIGNATURES = {
     "npb_energy": (_I, [_V, ctypes.POINTER(npb_opts), _dp]),
     "npb_energy_batch": (_I, [ctypes.POINTER(_V), _I32, ctypes.POINTER(npb_opts), ctypes.POINTER(ctypes.c_double)]),
     "npb_lod_run": (_I, [_V, ctypes.POINTER(npb_opts), _I32, _I32, _dp, _dp, _SZ]),
+    "npb_euler_run": (_I, [_V, ctypes.POINTER(npb_opts), _I32, _I32, _dp, _SZ]),
     "npb_potential": (_I, [_V, _I32, _dp, _SZ]),
     "npb_apply": (_I, [_V, ctypes.POINTER(npb_opts), _I32, _I32, _dp, _SZ]),
     "npb_grid_export": (_I, [_V, _I32, _V, _SZ]),
@@ -235,6 +236,13 @@ def npb_lod_run(grid: int, opts: npb_opts, leg: int, n_steps: int, u: np.ndarray
     src = None if source is None else np.ascontiguousarray(source, dtype=np.float64)
     _check(load_library().npb_lod_run(grid, ctypes.byref(opts), leg, n_steps, out.ctypes.data_as(_dp),
                                       None if src is None else src.ctypes.data_as(_dp), out.size))
+    return out
+
+
+def npb_euler_run(grid: int, opts: npb_opts, leg: int, n_steps: int, u: np.ndarray) -> np.ndarray:
+    """n explicit Euler steps of one leg from the dense FP64 state u (faces = Dirichlet data)."""
+    out = np.ascontiguousarray(u, dtype=np.float64).copy()
+    _check(load_library().npb_euler_run(grid, ctypes.byref(opts), leg, n_steps, out.ctypes.data_as(_dp), out.size))
     return out
 
 

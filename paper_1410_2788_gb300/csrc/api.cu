@@ -1042,6 +1042,53 @@ extern "C" int npb_lod_run(npb_grid *g, const npb_opts *o, int32_t leg, int32_t 
     return grid_check_err(g, st, 0);
 }
 
+// n explicit Euler steps of one leg from a caller-given state (the steady-state reference).
+extern "C" int npb_euler_run(npb_grid *g, const npb_opts *opts, int32_t leg, int32_t n_steps, double *u_inout,
+                             size_t n_elems) {
+    if (!g || !u_inout) return fail(NPB_EINVAL, "grid/u_inout is NULL");
+    int rc = check_opts(opts);
+    if (rc) return rc;
+    if (leg < 0 || leg > 3) return fail(NPB_EINVAL, "unknown leg %d", leg);
+    if (n_steps < 0) return fail(NPB_EINVAL, "n_steps < 0");
+    const size_t total = (size_t)g->geo.nx * g->geo.ny * g->geo.nz;
+    if (n_elems != total) return fail(NPB_EINVAL, "n_elems %zu != nx*ny*nz %zu", n_elems, total);
+    npb_opts o = *opts;
+    o.scheme = NPB_LODIE2;  // the leg constants with the full r = tau/h^2
+    CU(cudaSetDevice(g->ctx->device));
+    cudaStream_t st = g->ctx->stream;
+    if ((rc = grid_prepare(g, &o, st))) return rc;
+    const int slot = kLegSlot[leg];
+    const int prec = o.precision;
+    void *u = g->d_u[prec][slot];
+    const size_t sbytes = state_bytes(&g->geo.nx, prec);
+    const bool solvent = leg == NPB_LEG_SOLVENT_TAU || leg == NPB_LEG_SOLVENT_HALF;
+    const bool half = leg == NPB_LEG_SOLVENT_HALF || leg == NPB_LEG_VACUUM_HALF;
+    const double tau = (half ? 0.5 : 1.0) * o.dt / o.alpha;
+    void *tmp = nullptr, *work = nullptr;
+    if ((rc = g->ctx->alloc(&tmp, total * sizeof(double)))) return rc;
+    if ((rc = g->ctx->alloc(&work, sbytes))) {
+        g->ctx->release(tmp, total * sizeof(double));
+        return rc;
+    }
+    const LegDev *legs = g->d_legs[prec] + slot;
+    cudaError_t e = cudaMemcpyAsync(tmp, u_inout, total * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(u, 0, sbytes, st);
+    if (e == cudaSuccess) e = pad_state(prec, g->geo, (const double *)tmp, u, st);
+    for (int s = 0; s < n_steps && e == cudaSuccess; ++s) {
+        e = launch_euler_step(prec, legs, u, work, g->geo, solvent ? tau * g->kappa2 : 0.0, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(u, work, sbytes, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = launch_source(prec, legs, 1, g->geo.ny, g->geo.nz, st);
+    }
+    if (e == cudaSuccess) e = unpad_state(prec, g->geo, u, (double *)tmp, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(u_inout, tmp, total * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaStreamSynchronize(st);
+    g->ctx->release(tmp, total * sizeof(double));
+    g->ctx->release(work, sbytes);
+    if (e != cudaSuccess) return fail(NPB_ECUDA, "npb_euler_run failed: %s", cudaGetErrorString(e));
+    return NPB_OK;
+}
+
 extern "C" int npb_grid_export(npb_grid *g, int32_t what, void *host_out, size_t n_elems) {
     if (!g || !host_out) return fail(NPB_EINVAL, "grid/host_out is NULL");
     const size_t total = (size_t)g->geo.nx * g->geo.ny * g->geo.nz;

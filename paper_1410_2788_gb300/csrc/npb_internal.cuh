@@ -79,6 +79,9 @@ cudaError_t launch_nonlinear(int prec, const LegDev *legs_dev, int n_legs, int n
 cudaError_t launch_source(int prec, const LegDev *legs_dev, int n_legs, int ny, int nz,
                           cudaStream_t st);
 struct GridGeom;
+// One explicit Euler step of Eq. (TimeDepNPB) for one leg (*leg in device memory), in -> out.
+cudaError_t launch_euler_step(int prec, const LegDev *leg, const void *in, void *out, const GridGeom &g,
+                              double tau_kappa2, cudaStream_t st);
 // The explicit half step of the Crank-Nicolson sweeps along dir, in place, for n_legs legs.
 cudaError_t launch_cn_explicit(int prec, const LegDev *legs_dev, int n_legs, int dir, cudaStream_t st);
 // phi_m^LOD + phi_0^LOD - phi_0^FFT as dense FP64 (the recovered potential of Sec. 5.3).

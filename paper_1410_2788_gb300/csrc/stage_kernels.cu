@@ -116,6 +116,59 @@ __global__ void k_cn_explicit(const LegDev *__restrict__ legs, int dir) {
     }
 }
 
+// One explicit Euler step of Eq. (TimeDepNPB) (the reference the pseudo-time schemes are compared
+// with): out = w + sum_d [e_+ (w_+ - w) + e_- (w_- - w)] - tau kbar^2 sinh(w) (solvent nodes outside
+// the molecule) at interior nodes, e = r*eps at the half points (the leg's rE, r = tau/h^2, from the
+// node or half-point bits); faces copied.  The source tau*rho is added by the source stage after it.
+template <typename T>
+__global__ void k_euler_step(const LegDev *__restrict__ lgp, const T *__restrict__ in, T *__restrict__ out,
+                             double tau_kappa2) {
+    const LegDev &lg = *lgp;
+    const int nx = lg.nx, ny = lg.ny, nz = lg.nz, pitch = lg.pitch;
+    const int wpr = mask_words_per_row(pitch);
+    const T rE0 = (T)lg.rE[0], rE1 = (T)lg.rE[1], rE2 = (T)lg.rE[2];
+    const int64_t total = (int64_t)nz * ny * pitch;
+    auto node_in = [&](int i, int j, int k) -> uint32_t {
+        if (!lg.mask) return 1u;
+        return (lg.mask[((int64_t)k * ny + j) * wpr + (i >> 5)] >> (i & 31)) & 1u;
+    };
+    auto e_half = [&](int d, int i, int j, int k) -> T {  // half point (i,j,k) + 1/2 along d
+        if (lg.eps_mode && lg.half[d])
+            return ((lg.half[d][((int64_t)k * ny + j) * wpr + (i >> 5)] >> (i & 31)) & 1u) ? rE2 : rE0;
+        const uint32_t a = node_in(i, j, k);
+        const uint32_t b = node_in(i + (d == 0), j + (d == 1), k + (d == 2));
+        return (a & b) ? rE2 : ((a | b) ? rE1 : rE0);
+    };
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(p % pitch);
+        const int64_t r = p / pitch;
+        const int j = (int)(r % ny), k = (int)(r / ny);
+        if (i >= nx) continue;
+        const T w = in[p];
+        if (i == 0 || j == 0 || k == 0 || i == nx - 1 || j == ny - 1 || k == nz - 1) {
+            out[p] = w;
+            continue;
+        }
+        const int64_t sy = pitch, sz = (int64_t)pitch * ny;
+        T lap = e_half(0, i, j, k) * (in[p + 1] - w) + e_half(0, i - 1, j, k) * (in[p - 1] - w);
+        lap += e_half(1, i, j, k) * (in[p + sy] - w) + e_half(1, i, j - 1, k) * (in[p - sy] - w);
+        lap += e_half(2, i, j, k) * (in[p + sz] - w) + e_half(2, i, j, k - 1) * (in[p - sz] - w);
+        T v = w + lap;
+        if (lg.nl_on && !node_in(i, j, k)) v -= (T)tau_kappa2 * sinh(w);
+        out[p] = v;
+    }
+}
+
+cudaError_t launch_euler_step(int prec, const LegDev *leg, const void *in, void *out, const GridGeom &g,
+                              double tau_kappa2, cudaStream_t st) {
+    const int64_t total = (int64_t)g.nz * g.ny * g.pitch;
+    const int b = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    if (prec == 0) k_euler_step<double><<<b, 256, 0, st>>>(leg, (const double *)in, (double *)out, tau_kappa2);
+    else k_euler_step<float><<<b, 256, 0, st>>>(leg, (const float *)in, (float *)out, tau_kappa2);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_cn_explicit(int prec, const LegDev *legs, int n_legs, int dir, cudaStream_t st) {
     dim3 grid(152 * 4, 1, n_legs);
     if (prec == 0) k_cn_explicit<double><<<grid, 128, 0, st>>>(legs, dir);

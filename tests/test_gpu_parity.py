@@ -391,3 +391,26 @@ def test_lodcn_step_and_energy(npb, O, scheme, precision, tol):
         npb.npb_ctx_destroy(c)
     ref_dg = O.energy(p, 10.0, 6, scheme=scheme)
     assert abs(dg - ref_dg) <= tol * abs(ref_dg), (dg, ref_dg)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-4)])
+@pytest.mark.parametrize("leg", [0, 2])
+def test_explicit_euler_reference(npb, O, precision, tol, leg):
+    """npb_euler_run: explicit Euler steps of Eq. (TimeDepNPB) from the leg's initial state (solvent
+    and vacuum), against the oracle's Euler stepping, on the ragged molecule grid."""
+    p = small_molecule()
+    medium = O.SOLVENT if leg == 0 else O.VACUUM
+    st = O.setup(p, medium)
+    tau, n = 4e-4, 120
+    c = npb.npb_ctx_create(0, 0)
+    try:
+        g = npb.npb_grid_create(c, p)
+        try:
+            got = npb.npb_euler_run(g, npb.make_opts(tau, 1.0, n, precision=precision), leg, n, st.u0)
+        finally:
+            npb.npb_grid_destroy(g)
+    finally:
+        npb.npb_ctx_destroy(c)
+    ref = st.u0.copy()
+    O.euler_run(ref, st, tau, p.h, n)
+    assert linf_rel(got, ref) <= tol
