@@ -10,6 +10,8 @@ Tolerances:
 """
 import math
 
+import os
+
 import numpy as np
 import pytest
 
@@ -237,10 +239,13 @@ def test_energy_protein_1k_129(npb, ctx, O):
     """The 1,000-atom random-walk molecule on 129^3: RE+V at dt 0.4 / alpha 1/25, 25 steps."""
     rep = _energy_case(npb, ctx, O, I.protein_1k(), 0.4, 1.0 / 25.0, 25)
     print("protein_1k", rep)
-    import json, os
-    os.makedirs("gpurun_out", exist_ok=True)
-    with open("gpurun_out/fp32_error_protein_1k.json", "w") as f:
-        json.dump(rep, f, indent=1)
+    out = os.environ.get("NPB_REPORT_DIR")  # the FP32-vs-FP64 error report, when a directory is named
+    if out:
+        import json
+
+        os.makedirs(out, exist_ok=True)
+        with open(os.path.join(out, "fp32_error_protein_1k.json"), "w") as f:
+            json.dump(rep, f, indent=1)
 
 
 def test_energy_large_20k_257_fp32(npb, ctx, O):
