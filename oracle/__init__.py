@@ -16,7 +16,7 @@ legs into the solvation energy:
   * `vacuum_fft` - phi_0^FFT of Eq. (deltaG2): the vacuum Poisson problem solved directly with
                   the sine transform (Sec. 5.1); `energy_fft` - Eq. (deltaG2)
 
-Readings where the paper is silent (all stated in the design doc):
+Readings where the paper is silent:
   * C = e_c^2/(k_B T) = 332.0637 / 0.592183 A (Coulomb constant over kT at 298 K);
   * the discrete source is Q_p = 4 pi C qtilde_p / h^3 (Eq. RhoEq with a trilinear delta);
   * vacuum legs use eps = eps_in everywhere, kbar = 0 and Coulomb boundary data;
@@ -44,6 +44,7 @@ C_BJERRUM = COULOMB_KCAL_A / KT_KCAL  # e_c^2/(k_B T) in A at 298 K
 
 SOLVENT, VACUUM = 0, 1
 LODIE1, LODIE2, LODCN1, LODCN2 = 1, 2, 3, 4
+AOSIE1, AOSIE2, AOSCN1, AOSCN2, MAOSIE, MAOSCN = 5, 6, 7, 8, 9, 10
 
 
 def build(force: bool = False) -> str:
@@ -83,6 +84,7 @@ def _load():
     lib.or_source.argtypes = [i, i, i, dp, dp, d]
     lib.or_lod_run.argtypes = [i, i, i, dp, dp, dp, dp, dp, dp, d, d, i, i]
     lib.or_euler_run.argtypes = [i, i, i, dp, dp, dp, dp, dp, dp, dp, d, d, i]
+    lib.or_additive_run.argtypes = [i, i, i, dp, dp, dp, dp, dp, dp, dp, d, d, i, i]
     lib.or_set_threads.argtypes = [i]
     lib.or_get_threads.restype = i
     _lib = lib
@@ -241,8 +243,15 @@ def source(u: np.ndarray, rho: np.ndarray, tau: float) -> None:
 
 def lod_run(u: np.ndarray, st: Setup, tau: float, h: float, n_steps: int,
             scheme: int = LODIE2) -> None:
+    """n_steps of `scheme`: the LOD schemes of Sec. 3.1 (1-4) or the additive ones of
+    Sec. 3.2 / 3.3 (AOSIE1 ... MAOSCN, 5-10)."""
     nz, ny, nx = u.shape
     ex, ey, ez = st.e_half
+    if scheme >= AOSIE1:
+        work = np.empty((4,) + u.shape)
+        _load().or_additive_run(nx, ny, nz, _p(u), _p(work), _p(st.rho), _p(st.kappa2_node), _p(ex),
+                                _p(ey), _p(ez), tau, h, n_steps, scheme)
+        return
     _load().or_lod_run(nx, ny, nz, _p(u), _p(st.rho), _p(st.kappa2_node), _p(ex), _p(ey),
                        _p(ez), tau, h, n_steps, scheme)
 

@@ -21,6 +21,8 @@
  *   or_nonlinear         Eq. (ana3), the analytic solution of alpha w_t = -kbar^2 sinh w
  *   or_source            Eq. (LODIE1_5), u += dt/alpha * Q
  *   or_lod_run           LODIE1 (N,X,Y,Z,S), LODIE2 (S,X,Y,Z,N), LODCN1, LODCN2 steps (Sec. 3.1)
+ *   or_additive_run      AOSIE1/2, AOSCN1/2 (Sec. 3.2) and MAOSIE/MAOSCN (Sec. 3.3) steps: parts
+ *                        advanced side by side from one state and averaged
  *   or_euler_run         explicit Euler steps of Eq. (TimeDepNPB) (Sec. 5.2 reference)
  *
  * Layout: node (i,j,k) of an nx*ny*nz grid is stored at u[(k*ny + j)*nx + i];
@@ -209,19 +211,17 @@ void or_sweep(int nx, int ny, int nz, double *u, const double *e_half, int dir, 
     }
 }
 
-/* Eqs. (LODCN1_2)-(LODCN1_4): per line, the right-hand side is the explicit half step
- * w + (r/2) [e_{+1/2} (w_{t+1} - w_t) - e_{-1/2} (w_t - w_{t-1})] of the line's values (faces
- * included), then the implicit half step is the or_sweep solve with r/2. */
-void or_sweep_cn(int nx, int ny, int nz, double *u, const double *e_half, int dir, double r) {
+/* The explicit half of a Crank-Nicolson sweep along dir, in place at the interior nodes of every
+ * interior line: w_t + hr [e_{t+1/2} (w_{t+1} - w_t) - e_{t-1/2} (w_t - w_{t-1})], from the line's
+ * old values (faces included). */
+static void cn_explicit(int nx, int ny, int nz, double *u, const double *e_half, int dir, double hr) {
     const int n[3] = {nx, ny, nz};
     const int64_t stride[3] = {1, nx, (int64_t)nx * ny};
     const int len = n[dir];
     const int o1 = dir == 0 ? 1 : 0, o2 = dir == 2 ? 1 : 2;
-    const int m = len - 2;
-    if (m <= 0) return;
+    if (len - 2 <= 0) return;
     const int64_t s = stride[dir];
     const int n1 = n[o1], n2 = n[o2];
-    const double hr = 0.5 * r; /* r/2: each half step */
 #pragma omp parallel num_threads(g_threads)
     {
         double *w = (double *)malloc(sizeof(double) * (size_t)len);
@@ -242,7 +242,13 @@ void or_sweep_cn(int nx, int ny, int nz, double *u, const double *e_half, int di
             }
         free(w);
     }
-    or_sweep(nx, ny, nz, u, e_half, dir, hr);
+}
+
+/* Eqs. (LODCN1_2)-(LODCN1_4): per line, the right-hand side is the explicit half step with r/2,
+ * then the implicit half step is the or_sweep solve with r/2. */
+void or_sweep_cn(int nx, int ny, int nz, double *u, const double *e_half, int dir, double r) {
+    cn_explicit(nx, ny, nz, u, e_half, dir, 0.5 * r);
+    or_sweep(nx, ny, nz, u, e_half, dir, 0.5 * r);
 }
 
 /* Eq. (ana3) with a = kbar^2 dt / (2 alpha) = kbar^2 tau / 2:
@@ -303,6 +309,51 @@ void or_lod_run(int nx, int ny, int nz, double *u, const double *rho, const doub
         }
         if (first_n) or_source(nx, ny, nz, u, rho, tau);
         else or_nonlinear(nx, ny, nz, u, kappa2_node, tau);
+    }
+}
+
+/* n_steps of an additive splitting with tau = dt/alpha and r = tau/h^2 (Sec. 3.2, 3.3).
+ * AOS (schemes 5-8; Eqs. AOS1_1-5, AOS2_1-5): four parts advanced from U^n side by side -- the
+ *   nonlinear part alpha w_t = -4 kbar^2 sinh w integrated exactly (or_ana3 with a = 2 kbar^2 tau),
+ *   and one line solve per direction with 4r (implicit Euler, Eqs. AOSIE1_2-4 / AOSIE2_2-4) or with
+ *   2r on each side (Crank-Nicolson, Eqs. AOSCN1_2-4 / AOSCN2_2-4), its right-hand side carrying the
+ *   direction's share of the source: AOS1 4 tau Q on x alone, AOS2 4/3 tau Q on each direction;
+ *   U^{n+1} is the mean of the four.
+ * MAOS (schemes 9, 10; Eqs. MAOS1_1-5): the nonlinear stage (a = kbar^2 tau / 2) first, then three
+ *   line solves from its result with 3r (or 3r/2 on each side), each with tau Q; U^{n+1} is the
+ *   mean of the three.
+ * The source enters after the explicit half of a Crank-Nicolson solve.  work: 4 states. */
+void or_additive_run(int nx, int ny, int nz, double *u, double *work, const double *rho,
+                     const double *kappa2_node, const double *ex, const double *ey, const double *ez,
+                     double tau, double h, int n_steps, int scheme) {
+    const int64_t total = (int64_t)nx * ny * nz;
+    const int aos = scheme >= 5 && scheme <= 8;
+    const int cn = scheme == 7 || scheme == 8 || scheme == 10;
+    const double c = aos ? 4.0 : 3.0;
+    const double r = c * tau / (h * h);
+    double share[3] = {1.0, 1.0, 1.0};
+    if (scheme == 5 || scheme == 7) share[0] = 4.0, share[1] = share[2] = 0.0;
+    if (scheme == 6 || scheme == 8) share[0] = share[1] = share[2] = 4.0 / 3.0;
+    const double *e[3] = {ex, ey, ez};
+    double *w = work, *v[3] = {work + total, work + 2 * total, work + 3 * total};
+    for (int s = 0; s < n_steps; ++s) {
+        memcpy(w, u, sizeof(double) * (size_t)total);
+        or_nonlinear(nx, ny, nz, w, kappa2_node, aos ? 4.0 * tau : tau);
+        const double *from = aos ? u : w;
+        for (int d = 0; d < 3; ++d) {
+            memcpy(v[d], from, sizeof(double) * (size_t)total);
+            if (cn) cn_explicit(nx, ny, nz, v[d], e[d], d, 0.5 * r);
+            if (share[d] != 0.0) or_source(nx, ny, nz, v[d], rho, share[d] * tau);
+            or_sweep(nx, ny, nz, v[d], e[d], d, cn ? 0.5 * r : r);
+        }
+#pragma omp parallel for collapse(2) schedule(static) num_threads(g_threads)
+        for (int k = 1; k < nz - 1; ++k)
+            for (int j = 1; j < ny - 1; ++j)
+                for (int i = 1; i < nx - 1; ++i) {
+                    const int64_t p = idx3(i, j, k, nx, ny);
+                    u[p] = aos ? (w[p] + v[0][p] + v[1][p] + v[2][p]) / 4.0
+                               : (v[0][p] + v[1][p] + v[2][p]) / 3.0;
+                }
     }
 }
 
