@@ -57,6 +57,20 @@ extern "C" {
 #define NPB_LODIE1 1        /* N, X, Y, Z, S                                            */
 #define NPB_LODCN1 3        /* LODIE1's order with the Crank-Nicolson sweeps (Eqs. LODCN1_2-4) */
 #define NPB_LODCN2 4        /* LODIE2's order with the Crank-Nicolson sweeps            */
+/* Additive splittings (Sec. 3.2, 3.3): the parts advance side by side from one state and are
+ * averaged.  AOS: the nonlinear part (4 kbar^2, integrated exactly) and one line solve per
+ * direction from U^n with 4 tau (Crank-Nicolson: 2 tau on each side), mean of the four; the
+ * source goes to x alone (AOS*1) or a third to each direction (AOS*2).  MAOS: the nonlinear stage
+ * first, then three line solves from its result with 3 tau (CN: 3 tau/2 each side) and tau Q
+ * each, mean of the three.  Each leg uses three extra device states, allocated on first use
+ * (not counted by npb_grid_footprint).  npb_energy, npb_lod_solve, npb_lod_run and npb_apply
+ * (NPB_OP_STEP) run them; npb_energy_batch and npb_submit take the LOD schemes only. */
+#define NPB_AOSIE1 5        /* Eqs. AOSIE1_1-5                                          */
+#define NPB_AOSIE2 6        /* Eqs. AOSIE2_2-4 in place of AOSIE1_2-4                   */
+#define NPB_AOSCN1 7        /* Eqs. AOSCN1_2-4                                          */
+#define NPB_AOSCN2 8        /* Eqs. AOSCN2_2-4                                          */
+#define NPB_MAOSIE 9        /* Eqs. MAOS1_1-5, implicit Euler                          */
+#define NPB_MAOSCN 10       /* Eqs. MAOS1_1-5, Crank-Nicolson                          */
 
 #define NPB_FP64 0          /* every stage in FP64                                      */
 #define NPB_FP32_SWEEP 1    /* potential stored and swept in FP32; energy in FP64       */
@@ -81,7 +95,7 @@ extern "C" {
 #define NPB_OP_SWEEP_Y 2    /* y line solves                               Eq. (LODIE1_3) */
 #define NPB_OP_SWEEP_Z 3    /* z line solves                               Eq. (LODIE1_4) */
 #define NPB_OP_NONLINEAR 4  /* analytic sinh stage at solvent nodes        Eq. (ana3)     */
-#define NPB_OP_STEP 5       /* one full LOD step of opts->scheme                         */
+#define NPB_OP_STEP 5       /* one full step of opts->scheme                             */
 
 /* What npb_grid_export() copies out (dense nz*ny*nx arrays, x fastest). */
 #define NPB_EXPORT_MASK 0        /* uint8: 1 on/inside the molecular surface            */
@@ -118,7 +132,8 @@ typedef struct {
 typedef struct {
     double dt, alpha;
     int32_t n_steps;
-    int32_t scheme;           /* NPB_LODIE2 (default), NPB_LODIE1, NPB_LODCN1/2       */
+    int32_t scheme;           /* NPB_LODIE2 (default), NPB_LODIE1, NPB_LODCN1/2, or an
+                                 additive scheme NPB_AOSIE1 ... NPB_MAOSCN               */
     int32_t richardson;       /* 1: RE of Eq. (rich)                                   */
     int32_t vacuum_recovery;  /* 1: LOD vacuum legs of Eq. (deltaG3); 0: Eq. (deltaG2) */
     int32_t precision;        /* NPB_FP64 or NPB_FP32_SWEEP                            */
@@ -194,13 +209,14 @@ int npb_energy_batch(npb_grid *const *grids, int32_t n_grids, const npb_opts *op
  * (dimensionless), nz*ny*nx of them, x fastest.  n_elems must equal nx*ny*nz. */
 int npb_potential(npb_grid *grid, int32_t leg, double *host_out, size_t n_elems);
 
-/* n_steps LOD steps (Sec. 3.1, opts->scheme) of leg `leg` from a caller-given state, the
+/* n_steps steps of opts->scheme (Sec. 3.1-3.3) of leg `leg` from a caller-given state, the
  * pseudo-time run of Eq. (TimeDepNPB) with that leg's medium, eps at half points (opts->eps_mode)
  * and tau = dt/alpha (halved for the *_HALF legs).  u_inout: nz*ny*nx FP64 values of u, x
  * fastest; its interior is the initial value and its faces the Dirichlet data, which no stage
  * changes; the final state is copied back into it.  source (same layout, may be NULL) is a dense
  * source density rho: stage S then adds tau*rho at the interior nodes in place of the molecule's
- * point charges (the manufactured-solution benchmark of Sec. 4.1, Eqs. NPB_analytical_1/2);
+ * point charges (an additive scheme: each direction's share of it), the manufactured-solution
+ * benchmark of Sec. 4.1 (Eqs. NPB_analytical_1/2);
  * with NULL the step is the usual one with the charges.  n_elems must equal nx*ny*nz. */
 int npb_lod_run(npb_grid *grid, const npb_opts *opts, int32_t leg, int32_t n_steps, double *u_inout,
                 const double *source, size_t n_elems);

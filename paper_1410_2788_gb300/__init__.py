@@ -26,6 +26,7 @@ NPB_OK, NPB_PENDING = 0, 1
 NPB_EINVAL, NPB_ENOMEM, NPB_ECUDA, NPB_ETIMEOUT, NPB_ENOTFOUND, NPB_ESHUTDOWN = -1, -2, -3, -4, -5, -6
 NPB_SOLVENT, NPB_VACUUM = 0, 1
 NPB_LODIE1, NPB_LODIE2, NPB_LODCN1, NPB_LODCN2 = 1, 2, 3, 4
+NPB_AOSIE1, NPB_AOSIE2, NPB_AOSCN1, NPB_AOSCN2, NPB_MAOSIE, NPB_MAOSCN = 5, 6, 7, 8, 9, 10
 NPB_FP64, NPB_FP32_SWEEP = 0, 1
 NPB_EPS_HARMONIC, NPB_EPS_MIDPOINT = 0, 1
 NPB_LEG_SOLVENT_TAU, NPB_LEG_SOLVENT_HALF, NPB_LEG_VACUUM_TAU, NPB_LEG_VACUUM_HALF = 0, 1, 2, 3

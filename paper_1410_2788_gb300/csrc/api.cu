@@ -87,7 +87,8 @@ cudaError_t launch_sweep(int prec, int dir, const LegDev *legs, int n_legs, int 
 }
 
 const char *kKernelNames[K_COUNT] = {"sweep_x", "sweep_y", "sweep_z", "nonlinear", "source", "init_leg",
-                                     "energy", "setup_mask", "setup_charges", "setup_boundary", "pad", "cn_explicit"};
+                                     "energy", "setup_mask", "setup_charges", "setup_boundary", "pad", "cn_explicit",
+                                     "additive_combine"};
 }  // namespace npb
 
 // ------------------------------------------------------------------ context
@@ -496,7 +497,7 @@ LegDev npb::make_leg(const npb_grid *g, int leg, const npb_opts *o) {
     const double tau = (half ? 0.5 : 1.0) * o->dt / o->alpha;
     const double h = g->geo.h;
     // the Crank-Nicolson sweeps split r between their explicit and implicit halves (Eq. LODCN1_2)
-    const double r = tau / (h * h) * (o->scheme >= NPB_LODCN1 ? 0.5 : 1.0);
+    const double r = tau / (h * h) * (scheme_cn(o->scheme) ? 0.5 : 1.0);
     L.u = g->d_u[prec][kLegSlot[leg]];
     L.nx = g->geo.nx;
     L.ny = g->geo.ny;
@@ -538,7 +539,7 @@ static int check_opts(const npb_opts *o) {
     if (!o) return fail(NPB_EINVAL, "opts is NULL");
     if (!(o->dt > 0) || !(o->alpha > 0)) return fail(NPB_EINVAL, "dt and alpha must be > 0");
     if (o->n_steps < 0) return fail(NPB_EINVAL, "n_steps < 0");
-    if (o->scheme < NPB_LODIE1 || o->scheme > NPB_LODCN2) return fail(NPB_EINVAL, "unknown scheme %d", o->scheme);
+    if (o->scheme < NPB_LODIE1 || o->scheme > NPB_MAOSCN) return fail(NPB_EINVAL, "unknown scheme %d", o->scheme);
     if (o->precision != NPB_FP64 && o->precision != NPB_FP32_SWEEP)
         return fail(NPB_EINVAL, "unknown precision %d", o->precision);
     if (o->eps_mode != NPB_EPS_HARMONIC && o->eps_mode != NPB_EPS_MIDPOINT)
@@ -555,13 +556,14 @@ int npb::grid_prepare(npb_grid *g, const npb_opts *o, cudaStream_t st) {
     const int prec = o->precision;
     g->u_prec = prec;
     char key[256];
-    snprintf(key, sizeof key, "%.17g/%.17g/%d/%d", o->dt, o->alpha, o->eps_mode, o->scheme >= NPB_LODCN1 ? 1 : 0);
-    if (g->legs_key[prec] == key) return 0;
-    for (int leg = 0; leg < 4; ++leg) g->h_legs[prec][kLegSlot[leg]] = make_leg(g, leg, o);
-    CU(cudaMemcpyAsync(g->d_legs[prec], g->h_legs[prec], sizeof(LegDev) * 4, cudaMemcpyHostToDevice, st));
-    CU(cudaStreamSynchronize(st));
-    g->legs_key[prec] = key;
-    return 0;
+    snprintf(key, sizeof key, "%.17g/%.17g/%d/%d", o->dt, o->alpha, o->eps_mode, scheme_cn(o->scheme) ? 1 : 0);
+    if (g->legs_key[prec] != key) {
+        for (int leg = 0; leg < 4; ++leg) g->h_legs[prec][kLegSlot[leg]] = make_leg(g, leg, o);
+        CU(cudaMemcpyAsync(g->d_legs[prec], g->h_legs[prec], sizeof(LegDev) * 4, cudaMemcpyHostToDevice, st));
+        CU(cudaStreamSynchronize(st));
+        g->legs_key[prec] = key;
+    }
+    return scheme_additive(o->scheme) ? additive_prepare(g, o, st) : 0;
 }
 
 SweepShape npb::shape_for(npb_ctx *ctx, int prec, int dir, int n) {
@@ -659,7 +661,7 @@ int npb::step_legs(npb_ctx *ctx, const LegRef *refs, int n, const LegDev *d_tabl
     int rc;
     // Crank-Nicolson schemes: the first stage runs on its own (the explicit half step of x must see
     // its result), then each direction is the explicit half step followed by the implicit sweep
-    const bool cn = scheme >= NPB_LODCN1;
+    const bool cn = scheme_cn(scheme);
     const bool first_n = scheme == NPB_LODIE1 || scheme == NPB_LODCN1;
     // LODIE2's source stage: fused into the x sweep's load except by the kind-1 TMA kernel
     const bool src_apart = !first_n && (cn || (tma[0] && shape[0].kind == 1));
@@ -713,8 +715,9 @@ int npb::step_legs(npb_ctx *ctx, const LegRef *refs, int n, const LegDev *d_tabl
     return 0;
 }
 
-// One LOD step for legs [slot0, slot0 + n_legs) of one grid's leg table.
+// One step of `scheme` for legs [slot0, slot0 + n_legs) of one grid's leg table.
 int npb::run_step(npb_grid *g, int prec, int scheme, int slot0, int n_legs, cudaStream_t st) {
+    if (scheme_additive(scheme)) return additive_step(g, prec, scheme, slot0, n_legs, nullptr, st);
     LegRef refs[4];
     for (int i = 0; i < n_legs; ++i) refs[i] = {g, slot0 + i};
     return step_legs(g->ctx, refs, n_legs, g->d_legs[prec] + slot0, prec, scheme, st);
@@ -1017,12 +1020,16 @@ extern "C" int npb_lod_run(npb_grid *g, const npb_opts *o, int32_t leg, int32_t 
             if ((rc = run_step(g, prec, o->scheme, slot, 1, st))) return done(rc);
             continue;
         }
+        if (scheme_additive(o->scheme)) {  // each directional part adds its share of tau rho
+            if ((rc = additive_step(g, prec, o->scheme, slot, 1, src, st))) return done(rc);
+            continue;
+        }
         // the stages of Sec. 3.1 with S = u + tau rho: LODIE2/LODCN2 S, X, Y, Z, N;
         // LODIE1/LODCN1 N, X, Y, Z, S (Crank-Nicolson: each sweep after its explicit half step)
-        const bool cn = o->scheme >= NPB_LODCN1;
+        const bool cn = scheme_cn(o->scheme);
         const bool first_n = o->scheme == NPB_LODIE1 || o->scheme == NPB_LODCN1;
         const LegDev *legs = g->d_legs[prec] + slot;
-        if (!first_n) e = launch_add_interior(prec, g->geo, src, u, st);
+        if (!first_n) e = launch_add_interior(prec, g->geo, src, u, 1.0, st);
         else if (cn) e = launch_nonlinear(prec, legs, 1, n_dir[0], n_dir[1], n_dir[2], st);
         for (int d = 0; d < 3 && e == cudaSuccess; ++d) {
             int flags = 0;
@@ -1031,7 +1038,7 @@ extern "C" int npb_lod_run(npb_grid *g, const npb_opts *o, int32_t leg, int32_t 
             if (cn) e = launch_cn_explicit(prec, legs, 1, d, st);
             if (e == cudaSuccess) e = launch_dir(g, prec, d, shape_for(g->ctx, prec, d, n_dir[d]), slot, 1, flags, st);
         }
-        if (e == cudaSuccess && first_n) e = launch_add_interior(prec, g->geo, src, u, st);
+        if (e == cudaSuccess && first_n) e = launch_add_interior(prec, g->geo, src, u, 1.0, st);
         if (e != cudaSuccess) break;
     }
     if (e == cudaSuccess) e = unpad_state(prec, g->geo, u, (double *)tmp, st);

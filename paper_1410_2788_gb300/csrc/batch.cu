@@ -207,7 +207,8 @@ extern "C" int npb_energy_batch(npb_grid *const *grids, int32_t n_grids, const n
     if (!grids || n_grids <= 0 || !dG) return fail(NPB_EINVAL, "grids/dG is NULL or n_grids <= 0");
     if (!o) return fail(NPB_EINVAL, "opts is NULL");
     if (!(o->dt > 0) || !(o->alpha > 0) || o->n_steps < 0) return fail(NPB_EINVAL, "dt, alpha > 0, n_steps >= 0");
-    if (o->scheme < NPB_LODIE1 || o->scheme > NPB_LODCN2) return fail(NPB_EINVAL, "unknown scheme %d", o->scheme);
+    if (o->scheme < NPB_LODIE1 || o->scheme > NPB_LODCN2)
+        return fail(NPB_EINVAL, "npb_energy_batch runs the LOD schemes (1-4), not scheme %d", o->scheme);
     if (o->precision != NPB_FP64 && o->precision != NPB_FP32_SWEEP)
         return fail(NPB_EINVAL, "unknown precision %d", o->precision);
     if (!o->vacuum_recovery)

@@ -55,6 +55,16 @@ struct LegDev {
     const int2 *ent_xq;                  // charge entries as (x | y << 16, FP32 qtilde), ent_x's order
 };
 
+// One leg of an additive step (AOS/MAOS, Sec. 3.2-3.3): the states its combine stage reads.
+struct AddLeg {
+    void *u;                   // the leg's state: on entry the z part, on exit U^{n+1}
+    const void *a, *b, *c;     // U^n (AOS: the nonlinear part's start), the x part, the y part
+    const uint32_t *mask;      // node bits (the nonlinear part runs at solvent nodes outside)
+    int32_t nx, ny, nz, pitch;
+    int32_t nl_on;             // AOS: the nonlinear part runs (solvent legs with kbar > 0)
+    double q, omq;             // AOS: exp(-4 kbar^2 tau) and 1 - that
+};
+
 // Stage flags for the sweep kernels.
 enum : int {
     FUSE_PRE_SRC = 1,   // X sweep: add tau Q to the loaded line (LODIE2 stage S)
@@ -87,7 +97,11 @@ cudaError_t launch_cn_explicit(int prec, const LegDev *legs_dev, int n_legs, int
 // phi_m^LOD + phi_0^LOD - phi_0^FFT as dense FP64 (the recovered potential of Sec. 5.3).
 cudaError_t launch_recover(int prec, const GridGeom &g, const void *s_tau, const void *s_half, const void *v_tau,
                            const void *v_half, const double *vac, int richardson, double *out, cudaStream_t st);
-// u += src at the interior nodes of a padded state (dense source stage).
-cudaError_t launch_add_interior(int prec, const GridGeom &g, const void *src, void *u, cudaStream_t st);
+// u += scale * src at the interior nodes of a padded state (dense source stage).
+cudaError_t launch_add_interior(int prec, const GridGeom &g, const void *src, void *u, double scale,
+                                cudaStream_t st);
+// The last stage of an additive step for n_legs legs: U^{n+1} = (W + x + y + z)/4 (aos = 1, W the
+// nonlinear part from U^n) or (x + y + z)/3 (aos = 0), at interior nodes.
+cudaError_t launch_additive_combine(int prec, const AddLeg *legs_dev, int n_legs, int aos, cudaStream_t st);
 
 }  // namespace npb

@@ -23,7 +23,7 @@ constexpr int kMaxLine = 288;  // longest line the instantiated solver shapes co
 
 enum KernelKind {
     K_SWEEP_X = 0, K_SWEEP_Y, K_SWEEP_Z, K_NONLINEAR, K_SOURCE, K_INIT, K_ENERGY,
-    K_SETUP_MASK, K_SETUP_CHARGES, K_SETUP_BOUNDARY, K_PAD, K_CN_EXPLICIT, K_COUNT
+    K_SETUP_MASK, K_SETUP_CHARGES, K_SETUP_BOUNDARY, K_PAD, K_CN_EXPLICIT, K_COMBINE, K_COUNT
 };
 extern const char *kKernelNames[K_COUNT];
 
@@ -60,6 +60,13 @@ struct ServeState;  // serving scheduler (serve.cu)
 struct BatchPlan;   // npb_energy_batch plan (batch.cu)
 
 inline int64_t tune_key(int prec, int dir, int n) { return ((int64_t)prec << 40) | ((int64_t)dir << 32) | n; }
+
+// Schemes whose directional solves are Crank-Nicolson (legs carry r/2 per half step).
+inline bool scheme_cn(int s) {
+    return s == NPB_LODCN1 || s == NPB_LODCN2 || s == NPB_AOSCN1 || s == NPB_AOSCN2 || s == NPB_MAOSCN;
+}
+// The additive schemes of Sec. 3.2-3.3 (additive.cu).
+inline bool scheme_additive(int s) { return s >= NPB_AOSIE1 && s <= NPB_MAOSCN; }
 
 }  // namespace npb
 
@@ -119,6 +126,16 @@ struct npb_grid {
     npb::LegDev *d_legs[2] = {};       // device leg tables by precision
     npb::LegDev h_legs[2][4];
     std::string legs_key[2];
+    // additive schemes (additive.cu): per slot the saved U^n, the x part and the y part; the
+    // directional solves' legs [direction][slot]; the combine stage's legs; x/y tensor maps
+    void *d_aux[2][4][3] = {};
+    npb::LegDev h_sub[2][3][4];
+    npb::LegDev *d_sub[2] = {};
+    npb::AddLeg h_add[2][4];
+    npb::AddLeg *d_add[2] = {};
+    std::string add_key[2];
+    CUtensorMap tma_aux[2][3][4];  // [x | y][variant][slot]
+    bool tma_aux_built = false;
     double *d_vac_fft = nullptr;  // phi_0^FFT of Eq. (deltaG2), padded FP64 (fft_vacuum.cu)
     bool vac_fft_valid = false;
     int vac_fft_kind = -1;         // face flavour it was built from (0 FP64 pairs, 1 FP32 pairs)
@@ -185,6 +202,10 @@ int enqueue_energy(Grid *g, const npb_opts *o, cudaStream_t st);
 void serve_shutdown(Ctx *ctx);
 void batch_forget(Ctx *ctx, Grid *g);  // drop batch plans naming g (all plans when g is null)
 int grid_vacuum_fft(Grid *g, int prec, cudaStream_t st);  // phi_0^FFT into g->d_vac_fft
+// Additive schemes: the extra states and leg tables for opts (once per change), and one step of
+// legs [slot0, slot0 + n) (dense: a padded tau*rho in place of the charges, or null).
+int additive_prepare(Grid *g, const npb_opts *o, cudaStream_t st);
+int additive_step(Grid *g, int prec, int scheme, int slot0, int n, const void *dense, cudaStream_t st);
 
 }  // namespace npb
 

@@ -176,25 +176,63 @@ cudaError_t launch_cn_explicit(int prec, const LegDev *legs, int n_legs, int dir
     return cudaGetLastError();
 }
 
-// u += s at interior nodes, s a padded array in the state's layout (a dense source tau*rho).
+// u += scale * s at interior nodes, s a padded array in the state's layout (a dense source
+// tau*rho; scale = 1, or an additive scheme's share for one direction).
 template <typename T>
-__global__ void k_add_interior(GridGeom g, const T *__restrict__ src, T *__restrict__ u) {
+__global__ void k_add_interior(GridGeom g, const T *__restrict__ src, T *__restrict__ u, T scale) {
     const int64_t total = (int64_t)g.nz * g.ny * g.pitch;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
          p += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(p % g.pitch);
         const int64_t r = p / g.pitch;
         const int j = (int)(r % g.ny), k = (int)(r / g.ny);
-        if (i >= 1 && i <= g.nx - 2 && j >= 1 && j <= g.ny - 2 && k >= 1 && k <= g.nz - 2) u[p] += src[p];
+        if (i >= 1 && i <= g.nx - 2 && j >= 1 && j <= g.ny - 2 && k >= 1 && k <= g.nz - 2) u[p] += scale * src[p];
     }
 }
 
-cudaError_t launch_add_interior(int prec, const GridGeom &g, const void *src, void *u, cudaStream_t st) {
+cudaError_t launch_add_interior(int prec, const GridGeom &g, const void *src, void *u, double scale,
+                                cudaStream_t st) {
     const int64_t total = (int64_t)g.nz * g.ny * g.pitch;
     const int t = 256;
     const int b = (int)std::min<int64_t>((total + t - 1) / t, 152 * 16);
-    if (prec == 0) k_add_interior<double><<<b, t, 0, st>>>(g, (const double *)src, (double *)u);
-    else k_add_interior<float><<<b, t, 0, st>>>(g, (const float *)src, (float *)u);
+    if (prec == 0) k_add_interior<double><<<b, t, 0, st>>>(g, (const double *)src, (double *)u, scale);
+    else k_add_interior<float><<<b, t, 0, st>>>(g, (const float *)src, (float *)u, (float)scale);
+    return cudaGetLastError();
+}
+
+// The combine stage of an additive step (Eqs. AOS1_5 / AOS2_5 and MAOS1_5) at interior nodes, summed
+// in the order W, x, y, z.  AOS: W is the exact flow of alpha w_t = -4 kbar^2 sinh w over tau from
+// the saved U^n at solvent nodes (tanh(W/2) = exp(-4 kbar^2 tau) tanh(U^n/2)), U^n elsewhere.
+template <typename T>
+__global__ void k_additive_combine(const AddLeg *__restrict__ legs, int aos) {
+    const AddLeg *lg = legs + blockIdx.z;
+    T *u = static_cast<T *>(lg->u);
+    const T *a = static_cast<const T *>(lg->a), *b = static_cast<const T *>(lg->b),
+            *c = static_cast<const T *>(lg->c);
+    const int nx = lg->nx, ny = lg->ny, nz = lg->nz, pitch = lg->pitch, wpr = mask_words_per_row(pitch);
+    const int64_t total = (int64_t)(nz - 2) * (ny - 2) * (nx - 2);
+    const T q = (T)lg->q, omq = (T)lg->omq;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int i = 1 + (int)(p % (nx - 2));
+        const int64_t r = p / (nx - 2);
+        const int j = 1 + (int)(r % (ny - 2)), k = 1 + (int)(r / (ny - 2));
+        const int64_t row = (int64_t)k * ny + j, e = row * pitch + i;
+        if (aos) {
+            T w = a[e];
+            const bool inside = lg->mask ? ((lg->mask[row * wpr + (i >> 5)] >> (i & 31)) & 1u) : true;
+            if (lg->nl_on && !inside) w = nl_flow(w, q, omq);
+            u[e] = (((w + b[e]) + c[e]) + u[e]) * (T)0.25;
+        } else {
+            u[e] = ((b[e] + c[e]) + u[e]) / (T)3;
+        }
+    }
+}
+
+cudaError_t launch_additive_combine(int prec, const AddLeg *legs, int n_legs, int aos, cudaStream_t st) {
+    dim3 grid(152 * 4, 1, n_legs);
+    if (prec == 0) k_additive_combine<double><<<grid, 256, 0, st>>>(legs, aos);
+    else k_additive_combine<float><<<grid, 256, 0, st>>>(legs, aos);
     return cudaGetLastError();
 }
 

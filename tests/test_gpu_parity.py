@@ -419,3 +419,70 @@ def test_explicit_euler_reference(npb, O, precision, tol, leg):
     ref = st.u0.copy()
     O.euler_run(ref, st, tau, p.h, n)
     assert linf_rel(got, ref) <= tol
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-4)])
+@pytest.mark.parametrize("scheme", [5, 6, 7, 8, 9, 10])
+def test_additive_step_and_energy(npb, O, scheme, precision, tol):
+    """The additive schemes (AOSIE1/2, AOSCN1/2, MAOSIE, MAOSCN): one step from a random state
+    (row-level interface) and the RE+V energy (four legs per launch, then two) against the oracle
+    on the ragged 37x29x23 grid."""
+    p = small_molecule()
+    c = npb.npb_ctx_create(0, 0)
+    try:
+        g = npb.npb_grid_create(c, p)
+        try:
+            st = O.setup(p, O.SOLVENT)
+            rng = np.random.default_rng(91)
+            base = st.u0 + rng.normal(0, 4.0, st.u0.shape) * (st.u0 == 0)
+            if precision == 1:
+                base = base.astype(np.float32).astype(np.float64)
+            o = npb.make_opts(0.4, 0.04, 6, scheme=scheme, precision=precision)
+            got = npb.npb_apply(g, o, 0, npb.NPB_OP_STEP, base)
+            ref = base.copy()
+            O.lod_run(ref, st, 10.0, p.h, 1, scheme)
+            assert linf_rel(got, ref) <= tol
+            dg = npb.npb_energy(g, o)
+        finally:
+            npb.npb_grid_destroy(g)
+    finally:
+        npb.npb_ctx_destroy(c)
+    ref_dg = O.energy(p, 10.0, 6, scheme=scheme)
+    assert abs(dg - ref_dg) <= tol * abs(ref_dg), (dg, ref_dg)
+
+
+@pytest.mark.parametrize("scheme", [6, 10])
+def test_additive_midpoint_eps_energy(npb, O, scheme):
+    """Additive schemes with the midpoint eps reading (one-tile-per-block sweeps), FP64 and FP32."""
+    p = small_molecule()
+    c = npb.npb_ctx_create(0, 0)
+    try:
+        g = npb.npb_grid_create(c, p)
+        try:
+            dg = [npb.npb_energy(g, npb.make_opts(0.4, 0.04, 5, scheme=scheme, precision=prec,
+                                                  eps_mode=npb.NPB_EPS_MIDPOINT)) for prec in (0, 1)]
+        finally:
+            npb.npb_grid_destroy(g)
+    finally:
+        npb.npb_ctx_destroy(c)
+    ref_dg = O.energy(p, 10.0, 5, scheme=scheme, eps_mode="midpoint")
+    assert abs(dg[0] - ref_dg) <= 1e-10 * abs(ref_dg), (dg[0], ref_dg)
+    assert abs(dg[1] - ref_dg) <= 1e-4 * abs(ref_dg), (dg[1], ref_dg)
+
+
+def test_additive_schemes_rejected_by_batch_and_serving(npb):
+    """npb_energy_batch and npb_submit take the LOD schemes only."""
+    p = small_molecule()
+    c = npb.npb_ctx_create(0, 0)
+    try:
+        g = npb.npb_grid_create(c, p)
+        try:
+            o = npb.make_opts(0.4, 0.04, 2, scheme=npb.NPB_AOSIE2)
+            with pytest.raises(npb.NpbError):
+                npb.npb_energy_batch([g], o)
+            with pytest.raises(npb.NpbError):
+                npb.npb_submit(c, p, o)
+        finally:
+            npb.npb_grid_destroy(g)
+    finally:
+        npb.npb_ctx_destroy(c)

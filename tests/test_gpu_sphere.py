@@ -131,3 +131,62 @@ def test_sphere_reproduces_table2_lodcn(npb, h):
     ref_l2, ref_linf = _table2_lodcn()[h]
     assert abs(l2 - ref_l2) <= 0.006 * ref_l2, (h, l2, ref_l2)
     assert abs(linf - ref_linf) <= 0.006 * ref_linf, (h, linf, ref_linf)
+
+
+# --------------------------------------------------------------------------- AOS / MAOS (Sec. 3.2, 3.3)
+def _golden_cols(name):
+    rows = {}
+    for line in open(os.path.join(HERE, "golden", name)):
+        f = line.split()
+        if f and not line.startswith("#"):
+            rows[float(f[0])] = [float(v) for v in f[1:]]
+    return rows
+
+
+# scheme -> (golden table, column pair)
+ADDITIVE_ROWS = {5: ("paper_table3_aosie.txt", 0), 6: ("paper_table3_aosie.txt", 1),
+                 7: ("paper_table4_aoscn.txt", 0), 8: ("paper_table4_aoscn.txt", 1),
+                 9: ("paper_table5_maos.txt", 0), 10: ("paper_table5_maos.txt", 1)}
+
+
+@pytest.mark.parametrize("scheme", [5, 6, 7, 8, 9, 10])
+def test_sphere_additive_fp64_matches_oracle(npb, O, scheme):
+    """AOSIE1/2, AOSCN1/2, MAOSIE, MAOSCN on the GPU = the oracle, 1e-10 (h = 0.5, FP64)."""
+    _, u = gpu_sphere(npb, 0.5, scheme=scheme)
+    _, ref = sphere_case.run(0.5, scheme=scheme)
+    assert linf_rel(u, ref) <= 1e-10
+
+
+@pytest.mark.parametrize("eps_mode", ["midpoint", "harmonic"])
+@pytest.mark.parametrize("scheme", [5, 8, 10])
+def test_sphere_additive_fp32_matches_oracle(npb, O, scheme, eps_mode):
+    """FP32 additive steps (one-tile-per-block sweeps for midpoint eps, interior-row TMA sweeps on
+    the extra states for harmonic eps) against the FP64 oracle at h = 0.25, 1e-4 relative."""
+    _, u = gpu_sphere(npb, 0.25, precision=1, scheme=scheme, eps_mode=eps_mode)
+    st, exact, keep = sphere_case.build(0.25, 1.0, eps_mode)
+    ref = st.u0.copy()
+    dt = 0.25 * 0.25 / 20.0
+    O.lod_run(ref, st, dt, 0.25, int(round(10.0 / dt)), scheme)
+    assert linf_rel(u, ref) <= 1e-4
+
+
+@pytest.mark.parametrize("H", [1.0, 20.0])
+@pytest.mark.parametrize("scheme", [5, 8, 9, 10])
+def test_sphere_additive_table1_stable_at_dt5(npb, H, scheme):
+    """Table 1, rows AOS and MAOS: finite after 1e4 steps of dt = 5 (h = 0.25, FP32)."""
+    (l2, _), u = gpu_sphere(npb, 0.25, precision=1, scheme=scheme, dt=5.0, n_steps=10000, H=H)
+    assert np.all(np.isfinite(u)) and np.isfinite(l2) and l2 < 10.0
+
+
+@pytest.mark.parametrize("h", [0.125, 0.0625])
+@pytest.mark.parametrize("scheme", [5, 6, 7, 8, 9, 10])
+def test_sphere_reproduces_additive_tables(npb, h, scheme):
+    """Tables 3-5 at h = 0.125 and 0.0625 (49^3 and 97^3 grids, 12,800 and 51,200 steps), FP32
+    sweeps: the Crank-Nicolson columns (AOSCN1/2, MAOSCN1) to the printed three digits; the
+    implicit-Euler columns (AOSIE1/2, MAOSIE1) to the printed Linf digits and within 4% in L2."""
+    name, col = ADDITIVE_ROWS[scheme]
+    ref_l2, ref_linf = _golden_cols(name)[h][2 * col:2 * col + 2]
+    (l2, linf), _ = gpu_sphere(npb, h, precision=1, scheme=scheme)
+    tol_l2 = 0.006 if scheme in (7, 8, 10) else 0.04
+    assert abs(l2 - ref_l2) <= tol_l2 * ref_l2, (h, scheme, l2, ref_l2)
+    assert abs(linf - ref_linf) <= 0.006 * ref_linf, (h, scheme, linf, ref_linf)
