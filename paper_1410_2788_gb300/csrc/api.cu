@@ -132,27 +132,78 @@ int Profiler::collect() {
 }
 
 int Ctx::alloc(void **p, size_t bytes) {
-    if (bytes == 0) {
-        *p = nullptr;
-        return 0;
+    *p = nullptr;
+    if (bytes == 0) return 0;
+    const size_t sz = (bytes + 511) / 512 * 512;
+    std::lock_guard<std::mutex> lk(mem_mu);
+    const size_t cur = in_use.load();
+    if (cur + sz > budget)
+        return fail(NPB_ENOMEM, "HBM budget exceeded: %zu in use + %zu requested > %zu budget", cur, sz, budget);
+    auto it = cached.find(sz);
+    if (it != cached.end()) {
+        *p = it->second;
+        cached.erase(it);
+        cached_bytes -= sz;
+    } else {
+        if (cur + cached_bytes + sz > budget) trim();
+        cudaError_t e = cudaMalloc(p, sz);
+        if (e != cudaSuccess && cached_bytes) {  // the driver may be short of what the cache holds
+            cudaGetLastError();
+            trim();
+            e = cudaMalloc(p, sz);
+        }
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            *p = nullptr;
+            return fail(NPB_ENOMEM, "cudaMalloc(%zu) failed: %s", sz, cudaGetErrorString(e));
+        }
     }
-    size_t cur = in_use.load();
-    if (cur + bytes > budget)
-        return fail(NPB_ENOMEM, "HBM budget exceeded: %zu in use + %zu requested > %zu budget", cur, bytes,
-                    budget);
-    cudaError_t e = cudaMalloc(p, bytes);
-    if (e != cudaSuccess) {
-        *p = nullptr;
-        return fail(NPB_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
-    }
-    in_use += bytes;
+    live[*p] = sz;
+    in_use += sz;
     return 0;
 }
 
-void Ctx::release(void *p, size_t bytes) {
+// The block goes back to the cache.  Every caller has synchronised the streams that used it (the
+// same point at which cudaFree would have synchronised the device).
+void Ctx::release(void *p, size_t) {
     if (!p) return;
-    cudaFree(p);
-    in_use -= bytes;
+    std::lock_guard<std::mutex> lk(mem_mu);
+    auto it = live.find(p);
+    if (it == live.end()) return;
+    const size_t sz = it->second;
+    live.erase(it);
+    in_use -= sz;
+    cached.emplace(sz, p);
+    cached_bytes += sz;
+}
+
+void Ctx::trim() {
+    for (auto &c : cached) cudaFree(c.second);
+    cached.clear();
+    cached_bytes = 0;
+}
+
+int Ctx::pinned_slot(double **out) {
+    std::lock_guard<std::mutex> lk(mem_mu);
+    if (pinned_free.empty()) {
+        constexpr int kSlots = 64;
+        void *slab = nullptr;
+        if (cudaMallocHost(&slab, kSlots * 8 * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(NPB_ENOMEM, "cudaMallocHost failed");
+        }
+        pinned_slabs.push_back(slab);
+        for (int i = kSlots - 1; i >= 0; --i) pinned_free.push_back(static_cast<double *>(slab) + 8 * i);
+    }
+    *out = pinned_free.back();
+    pinned_free.pop_back();
+    return 0;
+}
+
+void Ctx::pinned_release(double *p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(mem_mu);
+    pinned_free.push_back(p);
 }
 
 extern "C" int npb_ctx_create(int device, size_t budget, npb_ctx **out) {
@@ -187,6 +238,12 @@ extern "C" void npb_ctx_destroy(npb_ctx *ctx) {
     cudaStreamSynchronize(ctx->stream);
     batch_forget(ctx, nullptr);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+    {
+        std::lock_guard<std::mutex> lk(ctx->mem_mu);
+        ctx->trim();
+        for (auto &l : ctx->live) cudaFree(l.first);  // blocks a caller never released
+        for (void *s : ctx->pinned_slabs) cudaFreeHost(s);
+    }
     delete ctx;
 }
 
@@ -297,7 +354,7 @@ void npb::grid_free(npb_grid *g) {
         if (c.exec) cudaGraphExecDestroy(c.exec);
     }
     for (auto &a : g->allocs) g->ctx->release(a.p, a.bytes);
-    if (g->h_result) cudaFreeHost(g->h_result);
+    g->ctx->pinned_release(g->h_result);
     delete g;
 }
 
@@ -344,10 +401,7 @@ int npb::grid_build(npb_ctx *ctx, const npb_problem *p, cudaStream_t st, npb_gri
     if ((rc = galloc(g, &g->d_result, 8))) return guard(rc);
     if ((rc = galloc(g, &g->d_err, 4))) return guard(rc);
     CU(cudaMemsetAsync(g->d_err, 0, 4 * sizeof(int32_t), st));
-    if (cudaMallocHost(&g->h_result, 8 * sizeof(double)) != cudaSuccess) {
-        g->h_result = nullptr;
-        return guard(fail(NPB_ENOMEM, "cudaMallocHost failed"));
-    }
+    if ((rc = ctx->pinned_slot(&g->h_result))) return guard(rc);
     if (na > 0) {
         CU(cudaMemcpyAsync(g->d_xyz, p->xyz, sizeof(double) * 3 * na, cudaMemcpyHostToDevice, st));
         CU(cudaMemcpyAsync(g->d_q, p->q, sizeof(double) * na, cudaMemcpyHostToDevice, st));
@@ -838,7 +892,12 @@ extern "C" int npb_energy(npb_grid *g, const npb_opts *o, double *dG) {
         GraphCache *hit = nullptr;
         for (auto &c : g->graphs)
             if (c.key == key && c.stream == st) hit = &c;
-        if (!hit) {
+        // A solve seen for the first time runs as direct launches (the launches overlap the GPU
+        // work); the graph is captured when the same solve comes back, where replay pays off.
+        const std::string seen = std::string(key) + "@" + std::to_string((uintptr_t)st);
+        if (!hit && g->seen.insert(seen).second) {
+            if ((rc = enqueue_energy(g, o, st))) return rc;
+        } else if (!hit) {
             cudaGraph_t graph;
             CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
             rc = enqueue_energy(g, o, st);
@@ -857,7 +916,7 @@ extern "C" int npb_energy(npb_grid *g, const npb_opts *o, double *dG) {
             g->graphs.push_back(c);
             hit = &g->graphs.back();
         }
-        CU(cudaGraphLaunch(hit->exec, st));
+        if (hit) CU(cudaGraphLaunch(hit->exec, st));
     } else {
         if ((rc = enqueue_energy(g, o, st))) return rc;
     }

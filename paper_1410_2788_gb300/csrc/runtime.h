@@ -6,6 +6,7 @@
 #include <deque>
 #include <map>
 #include <mutex>
+#include <set>
 #include <string>
 #include <thread>
 #include <vector>
@@ -84,8 +85,21 @@ struct npb_ctx {
     npb::ServeState *serve = nullptr;
     std::mutex batch_mu;
     std::vector<npb::BatchPlan *> batches;  // npb_energy_batch plans: leg tables and graphs
+    // Device memory: released blocks are kept by size and handed to later requests of the same
+    // size (grids of one shape come and go in serving and one-shot use); they count against the
+    // budget and are returned to the driver when a request would not fit otherwise.
+    std::mutex mem_mu;
+    std::multimap<size_t, void *> cached;
+    std::map<void *, size_t> live;
+    size_t cached_bytes = 0;
     int alloc(void **p, size_t bytes);
     void release(void *p, size_t bytes);
+    void trim();  // caller holds mem_mu
+    // Pinned host slots of 8 doubles for result read-backs, carved from shared slabs.
+    std::vector<double *> pinned_free;
+    std::vector<void *> pinned_slabs;
+    int pinned_slot(double **out);
+    void pinned_release(double *p);
 };
 
 namespace npb {
@@ -154,6 +168,7 @@ struct npb_grid {
     npb::ChargeScratch sc{};
     std::vector<npb::Alloc> allocs;
     std::vector<npb::GraphCache> graphs;
+    std::set<std::string> seen;  // solves run once already (captured as a graph the next time)
 };
 
 namespace npb {

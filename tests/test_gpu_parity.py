@@ -295,7 +295,8 @@ def test_invalid_arguments(npb, ctx):
     assert e.value.code == npb.NPB_EINVAL
     g = npb.npb_grid_create(ctx, p)
     try:
-        for o in [npb.make_opts(-0.1, 1.0, 5), npb.make_opts(0.1, 0.0, 5), npb.make_opts(0.1, 1.0, 5, scheme=7)]:
+        for o in [npb.make_opts(-0.1, 1.0, 5), npb.make_opts(0.1, 0.0, 5), npb.make_opts(0.1, 1.0, 5, scheme=11),
+                  npb.make_opts(0.1, 1.0, 5, scheme=0)]:
             with pytest.raises(npb.NpbError) as e:
                 npb.npb_energy(g, o)
             assert e.value.code == npb.NPB_EINVAL
