@@ -713,27 +713,34 @@ int npb::step_legs(npb_ctx *ctx, const LegRef *refs, int n, const LegDev *d_tabl
     }
     cudaEvent_t ev{};
     int rc;
-    // Crank-Nicolson schemes: the first stage runs on its own (the explicit half step of x must see
-    // its result), then each direction is the explicit half step followed by the implicit sweep
+    // Crank-Nicolson schemes: each direction is the explicit half step followed by the implicit
+    // sweep; the first stage (S or N) comes before the x half step (fused into its load, or a launch
+    // of its own where the half step is a launch of its own)
     const bool cn = scheme_cn(scheme);
     const bool first_n = scheme == NPB_LODIE1 || scheme == NPB_LODCN1;
-    // LODIE2's source stage: fused into the x sweep's load except by the kind-1 TMA kernel
-    const bool src_apart = !first_n && (cn || (tma[0] && shape[0].kind == 1));
+    // Crank-Nicolson: the interior-row kernels take the explicit half step on their loaded lines
+    // (after a fused S); elsewhere it is its own launch before each sweep
+    bool cn_fused = cn;
+    for (int d = 0; d < 3; ++d) cn_fused = cn_fused && tma[d] && shape[d].kind == 2;
+    // LODIE2's source stage: fused into the x sweep's load except by the kind-1 TMA kernel and before
+    // an explicit half step of its own launch
+    const bool src_apart = !first_n && ((cn && !cn_fused) || (tma[0] && shape[0].kind == 1));
     if (src_apart) {
         if ((rc = pr.begin(st, &ev))) return rc;
         CU(launch_source(prec, d_table, n, ny, nz, st));
         if ((rc = pr.end(st, ev, K_SOURCE))) return rc;
     }
-    if (cn && first_n) {
+    if (cn && first_n && !cn_fused) {
         if ((rc = pr.begin(st, &ev))) return rc;
         CU(launch_nonlinear(prec, d_table, n, nx, ny, nz, st));
         if ((rc = pr.end(st, ev, K_NONLINEAR))) return rc;
     }
     for (int d = 0; d < 3; ++d) {
         int flags = 0;
-        if (d == 0 && !cn) flags = !first_n ? (src_apart ? 0 : FUSE_PRE_SRC) : FUSE_PRE_NL;
+        if (d == 0 && (!cn || cn_fused)) flags = !first_n ? (src_apart ? 0 : FUSE_PRE_SRC) : FUSE_PRE_NL;
         if (d == 2 && !first_n) flags = FUSE_POST_NL;
-        if (cn) {
+        if (cn_fused) flags |= FUSE_PRE_CN;
+        if (cn && !cn_fused) {
             if ((rc = pr.begin(st, &ev))) return rc;
             CU(launch_cn_explicit(prec, d_table, n, d, st));
             if ((rc = pr.end(st, ev, K_CN_EXPLICIT))) return rc;

@@ -70,6 +70,8 @@ enum : int {
     FUSE_PRE_SRC = 1,   // X sweep: add tau Q to the loaded line (LODIE2 stage S)
     FUSE_PRE_NL = 2,    // X sweep: nonlinear stage on the loaded line (LODIE1 stage N)
     FUSE_POST_NL = 4,   // Z sweep: nonlinear stage before the store (LODIE2 stage N)
+    FUSE_PRE_CN = 8,    // interior-row sweeps: the explicit half of a Crank-Nicolson sweep on the
+                        // loaded lines (after a fused S), the leg's r*eps already halved
 };
 
 struct SweepShape {     // one instantiated line-solver shape

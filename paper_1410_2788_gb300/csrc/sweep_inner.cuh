@@ -129,7 +129,9 @@ constexpr int inner_min_blocks() {
     return NT >= 256 ? (1024 / NT > 0 ? 1024 / NT : 1) : (768 / NT > 0 ? 768 / NT : 1);
 }
 
-template <int DIR, int TX, int SEG, int L, bool TABLE>
+// CN: the explicit half of a Crank-Nicolson sweep on the loaded lines (flag FUSE_PRE_CN), compiled
+// as its own variant so that the implicit-Euler sweeps carry none of its code.
+template <int DIR, int TX, int SEG, int L, bool TABLE, bool CN = false>
 __global__ void __launch_bounds__(TX *SEG, inner_min_blocks<TX * SEG>())
     sweep_inner_kernel(const __grid_constant__ TmaLaunch P, int flags) {
     using T = float;
@@ -274,6 +276,7 @@ __global__ void __launch_bounds__(TX *SEG, inner_min_blocks<TX * SEG>())
         const bool nl_on = lg.nl_on != 0;
         const bool pre_nl = (flags & FUSE_PRE_NL) && nl_on;
         const bool post_nl = (flags & FUSE_POST_NL) && nl_on;
+        constexpr bool pre_cn = CN;
         T *D = data(s);
         const bool active = DIR == DIR_X ? (1 + a * TX + line <= lg.ny - 2)
                                          : (a * TX + line >= 1 && a * TX + line <= lg.nx - 2);
@@ -298,7 +301,7 @@ __global__ void __launch_bounds__(TX *SEG, inner_min_blocks<TX * SEG>())
         if (src_next) src_range(sn, ntb, nte);
         // row n-2 of the line: move its face coupling eps u_{n-1} to the right-hand side (after
         // the inflowing nonlinear stage, so the flow sees the bare node value)
-        if (nrem >= 1 && nrem <= L) {
+        if (!pre_cn && nrem >= 1 && nrem <= L) {  // (Crank-Nicolson: in registers after the explicit half)
             const int k = nrem - 1;
             T v = D[at(g0 + k)];
             if (pre_nl && ((flow >> k) & 1u)) v = nl_flow(v, nlq, nlomq);
@@ -319,6 +322,37 @@ __global__ void __launch_bounds__(TX *SEG, inner_min_blocks<TX * SEG>())
 #pragma unroll
                 for (int k = 0; k < L; ++k)
                     if ((flow >> k) & 1u) al[k] = nl_flow(al[k], nlq, nlomq);
+            }
+            if constexpr (pre_cn) {
+                // the explicit half w_k + e_{k+1/2} (w_{k+1} - w_k) - e_{k-1/2} (w_k - w_{k-1}) from the
+                // staged values (no thread writes the tile before the elimination's first barrier);
+                // the neighbours beyond the segment and the top face come from shared memory
+                T wprev = nrem > 0 ? D[at(g0 - 1)] : T(0);
+                T wtop = nrem >= L ? D[at(g0 + L)] : T(0);
+                if (pre_nl) {  // LODCN1: the neighbours take the inflowing nonlinear stage too
+                    if (seg > 0 && nrem > 0 && !(nb & 1u)) wprev = nl_flow(wprev, nlq, nlomq);
+                    if (nrem > L && !((nb >> (L + 1)) & 1u)) wtop = nl_flow(wtop, nlq, nlomq);
+                }
+                if (!FULL) {
+#pragma unroll
+                    for (int k = 0; k < L; ++k)
+                        if (k == nrem) al[k] = D[at(g0 + k)];  // the face u_{n-1} above the last unknown
+                }
+#pragma unroll
+                for (int k = 0; k < L; ++k) {
+                    const T w = al[k];
+                    const T wn = k + 1 < L ? al[k + 1] : wtop;
+                    const T v = w + eh(k + 1) * (wn - w) - eh(k) * (w - wprev);
+                    wprev = w;
+                    al[k] = (FULL || k < nrem) ? v : T(0);
+                }
+                if (nrem >= 1 && nrem <= L) {  // row n-2: its face coupling eps u_{n-1} to the right-hand side
+                    const T etop = ((both >> nrem) & 1u) ? rE2 : (((any >> nrem) & 1u) ? rE1 : rE0);
+                    const T face = D[at(g0 + nrem)];
+#pragma unroll
+                    for (int k = 0; k < L; ++k)
+                        if (k == nrem - 1) al[k] = fmaf(etop, face, al[k]);
+                }
             }
             // row 0 (F) coefficients, then the forward elimination over rows 1 .. L-2 with x_0 = F
             const T em0 = eh(0), ep0 = eh(1);

@@ -21,17 +21,21 @@ static cudaError_t launch_inner_shape(const TmaLaunch &P, const TmaGeom &g, int 
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
     if (DIR != DIR_X && g.nload > 1 && tma_data_box_bytes(g.rows, TX) % 128) return cudaErrorInvalidValue;
     const bool table = P.table != nullptr;
-    auto kern = table ? sweep_inner_kernel<DIR, TX, SEG, L, true> : sweep_inner_kernel<DIR, TX, SEG, L, false>;
+    const bool cn = (flags & FUSE_PRE_CN) != 0;
+    if (table && cn) return cudaErrorInvalidValue;  // table launches run the implicit-Euler schemes
+    const int variant = table ? 1 : (cn ? 2 : 0);
+    auto kern = table ? sweep_inner_kernel<DIR, TX, SEG, L, true>
+                      : (cn ? sweep_inner_kernel<DIR, TX, SEG, L, false, true> : sweep_inner_kernel<DIR, TX, SEG, L, false>);
     static std::mutex mu;
-    static std::map<std::pair<size_t, bool>, int> occ;
+    static std::map<std::pair<size_t, int>, int> occ;
     int per_sm = 0;
     {
         std::lock_guard<std::mutex> lk(mu);
-        auto it = occ.find({smem, table});
+        auto it = occ.find({smem, variant});
         if (it == occ.end()) {
             cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX * SEG, smem);
             if (e != cudaSuccess) return e;
-            occ[{smem, table}] = per_sm;
+            occ[{smem, variant}] = per_sm;
         } else {
             per_sm = it->second;
         }
@@ -67,7 +71,8 @@ static cudaError_t prepare_inner_dir() {
 #define NPB_INNER_PREP(SEG_, L_)                                                                                  \
     if (e == cudaSuccess)                                                                                      \
         e = prepare_inner_kernel(sweep_inner_kernel<DIR, TX, SEG_, L_, false>);                                \
-    if (e == cudaSuccess) e = prepare_inner_kernel(sweep_inner_kernel<DIR, TX, SEG_, L_, true>);
+    if (e == cudaSuccess) e = prepare_inner_kernel(sweep_inner_kernel<DIR, TX, SEG_, L_, true>);              \
+    if (e == cudaSuccess) e = prepare_inner_kernel(sweep_inner_kernel<DIR, TX, SEG_, L_, false, true>);
     if constexpr (TX == 8) { NPB_INNER_SEGS_X(NPB_INNER_PREP) } else { NPB_INNER_SEGS_YZ(NPB_INNER_PREP) }
 #undef NPB_INNER_PREP
     return e;

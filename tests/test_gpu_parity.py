@@ -94,11 +94,13 @@ def test_stage_parity(npb, ctx, O, precision, tol, leg, scheme):
 
 
 @pytest.mark.parametrize("shape", range(22))
-@pytest.mark.parametrize("leg,scheme", [(0, 2), (2, 2), (1, 1), (3, 1)])
+@pytest.mark.parametrize("leg,scheme", [(0, 2), (2, 2), (1, 1), (3, 1), (0, 4), (1, 3)])
 def test_inner_sweep_stage_parity(npb, O, shape, leg, scheme):
     """The interior-row FP32 sweeps (kind 2) pinned for all three directions on the ragged
     37x29x23 grid: the last unknown of a line falls on a segment's first row (x, L = 17;
-    y, L = 13), its last row (y, L = 9) and inside it, with whole padding segments above."""
+    y, L = 13), its last row (y, L = 9) and inside it, with whole padding segments above.
+    LODCN2/LODCN1 steps run the explicit half steps fused into the sweeps' loads (LODCN1 with the
+    nonlinear stage fused before them)."""
     c = npb.npb_ctx_create(0, 0)
     try:
         p = small_molecule()
@@ -131,9 +133,9 @@ def _stage_check(npb, ctx, O, precision, tol, leg, scheme):
             ref = base.copy()
             if name == "SOURCE":
                 O.source(ref, st.rho, tau)
-            elif name.startswith("SWEEP"):
+            elif name.startswith("SWEEP"):  # the implicit solve (a Crank-Nicolson leg's is the half with tau/2)
                 d = "XYZ".index(name[-1])
-                O.sweep(ref, st.e_half[d], d, tau, p.h)
+                O.sweep(ref, st.e_half[d], d, tau * (0.5 if scheme in (3, 4) else 1.0), p.h)
             elif name == "NONLINEAR":
                 O.nonlinear(ref, st.kappa2_node, tau)
             else:
