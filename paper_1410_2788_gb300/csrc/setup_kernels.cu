@@ -13,6 +13,8 @@
 //
 // The distance tests and weights use explicitly rounded FP64 operations (no fused
 // multiply-add), so that inside/outside decisions and node charges are reproducible.
+#include <algorithm>
+
 #include "npb_internal.cuh"
 #include "setup_kernels.cuh"
 
@@ -26,12 +28,14 @@ __device__ __forceinline__ double dist2(double dx, double dy, double dz) {
     return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
 }
 
-// One block per atom; threads walk the atom's bounding box of nodes.
+// One block per atom.  A thread owns one 32-node word of an x-row (j, k) of the atom's bounding box,
+// decides its nodes one by one (the oracle's distance test, in the same FP64 operations), and sets
+// them with one atomicOr per array: the node mask and, for the midpoint reading, the three
+// half-point arrays.
 __global__ void k_mask_atoms(GridGeom g, const double *__restrict__ xyz,
                              const double *__restrict__ radius, int n_atoms,
                              uint32_t *__restrict__ mask, uint32_t *__restrict__ hx,
-                             uint32_t *__restrict__ hy, uint32_t *__restrict__ hz,
-                             uint32_t *__restrict__ my, uint32_t *__restrict__ mz) {
+                             uint32_t *__restrict__ hy, uint32_t *__restrict__ hz) {
     const int a = blockIdx.x;
     if (a >= n_atoms) return;
     const double c[3] = {xyz[3 * a], xyz[3 * a + 1], xyz[3 * a + 2]};
@@ -48,30 +52,85 @@ __global__ void k_mask_atoms(GridGeom g, const double *__restrict__ xyz,
     }
     const int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1, ez = hi[2] - lo[2] + 1;
     if (ex <= 0 || ey <= 0 || ez <= 0) return;
-    const int total = ex * ey * ez;
+    const int w0 = lo[0] >> 5, nw = (hi[0] >> 5) - w0 + 1;
+    const int total = nw * ey * ez;
     const int wpr = mask_words_per_row(g.pitch);
-    const int wy = line_words(g.ny), wz = line_words(g.nz);
     const double hh = __dmul_rn(0.5, g.h);
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        const int i = lo[0] + t % ex;
-        const int j = lo[1] + (t / ex) % ey;
-        const int k = lo[2] + t / (ex * ey);
-        const double px = node_coord(o[0], i, g.h), py = node_coord(o[1], j, g.h),
-                     pz = node_coord(o[2], k, g.h);
-        const int64_t w = ((int64_t)k * g.ny + j) * wpr + (i >> 5);
-        const uint32_t bit = 1u << (i & 31);
-        if (dist2(__dsub_rn(px, c[0]), __dsub_rn(py, c[1]), __dsub_rn(pz, c[2])) <= r2) {
-            atomicOr(mask + w, bit);
-            if (my) atomicOr(my + ((int64_t)k * g.nx + i) * wy + (j >> 5), 1u << (j & 31));
-            if (mz) atomicOr(mz + ((int64_t)j * g.nx + i) * wz + (k >> 5), 1u << (k & 31));
+        const int wi = w0 + t % nw;
+        const int j = lo[1] + (t / nw) % ey;
+        const int k = lo[2] + t / (nw * ey);
+        const int ib = max(lo[0], wi * 32), ie = min(hi[0], wi * 32 + 31);
+        const double py = node_coord(o[1], j, g.h), pz = node_coord(o[2], k, g.h);
+        // An FP32 estimate of the squared distance decides every node outside a relative band of
+        // 1e-5 around r^2 (its error is below 1e-6 of d^2); inside the band the FP64 test decides.
+        const float dyf = (float)__dsub_rn(py, c[1]), dzf = (float)__dsub_rn(pz, c[2]);
+        const float dx0 = (float)__dsub_rn(node_coord(o[0], ib, g.h), c[0]), hf = (float)g.h, hhf = (float)hh;
+        const float r2f = (float)r2, lo_band = r2f * (1.f - 1e-5f), hi_band = r2f * (1.f + 1e-5f);
+        auto inside = [&](float ex2, int i, int axis) -> bool {  // ex2: FP32 d^2 of the point
+            if (ex2 < lo_band) return true;
+            if (ex2 > hi_band) return false;
+            double px = node_coord(o[0], i, g.h), qy = py, qz = pz;
+            if (axis == 0) px = __dadd_rn(px, hh);
+            if (axis == 1) qy = __dadd_rn(qy, hh);
+            if (axis == 2) qz = __dadd_rn(qz, hh);
+            return dist2(__dsub_rn(px, c[0]), __dsub_rn(qy, c[1]), __dsub_rn(qz, c[2])) <= r2;
+        };
+        const float yz2 = fmaf(dyf, dyf, dzf * dzf);
+        uint32_t m = 0, mx = 0, my = 0, mz = 0;
+        for (int i = ib; i <= ie; ++i) {
+            const float dxf = fmaf((float)(i - ib), hf, dx0);
+            const uint32_t bit = 1u << (i & 31);
+            if (inside(fmaf(dxf, dxf, yz2), i, -1)) m |= bit;
+            if (hx) {
+                const float dxh = dxf + hhf, dyh = dyf + hhf, dzh = dzf + hhf;
+                if (inside(fmaf(dxh, dxh, yz2), i, 0)) mx |= bit;
+                if (inside(fmaf(dxf, dxf, fmaf(dyh, dyh, dzf * dzf)), i, 1)) my |= bit;
+                if (inside(fmaf(dxf, dxf, fmaf(dyf, dyf, dzh * dzh)), i, 2)) mz |= bit;
+            }
         }
-        if (hx) {
-            if (dist2(__dsub_rn(__dadd_rn(px, hh), c[0]), __dsub_rn(py, c[1]), __dsub_rn(pz, c[2])) <= r2)
-                atomicOr(hx + w, bit);
-            if (dist2(__dsub_rn(px, c[0]), __dsub_rn(__dadd_rn(py, hh), c[1]), __dsub_rn(pz, c[2])) <= r2)
-                atomicOr(hy + w, bit);
-            if (dist2(__dsub_rn(px, c[0]), __dsub_rn(py, c[1]), __dsub_rn(__dadd_rn(pz, hh), c[2])) <= r2)
-                atomicOr(hz + w, bit);
+        const int64_t w = ((int64_t)k * g.ny + j) * wpr + wi;
+        if (m) atomicOr(mask + w, m);
+        if (mx) atomicOr(hx + w, mx);
+        if (my) atomicOr(hy + w, my);
+        if (mz) atomicOr(hz + w, mz);
+    }
+}
+
+// The line-major copies of the node mask -- bit y of line (x, z) into my, bit z of line (x, y)
+// into mz -- as 32 x 32 bit transposes of the x-row mask, one tile per warp: lane l loads the word
+// of row l of the tile, and a ballot over the lanes gathers each column.
+__global__ void k_mask_transpose(GridGeom g, const uint32_t *__restrict__ mask, uint32_t *__restrict__ my,
+                                 uint32_t *__restrict__ mz) {
+    const int lane = threadIdx.x & 31;
+    const int wpr = mask_words_per_row(g.pitch);
+    const int xw = (g.nx + 31) >> 5, ty = (g.ny + 31) >> 5, tz = (g.nz + 31) >> 5;
+    const int64_t n_y = (int64_t)g.nz * ty * xw, n_z = (int64_t)g.ny * tz * xw;
+    const int wy = line_words(g.ny), wz = line_words(g.nz);
+    for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile < n_y + n_z;
+         tile += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const bool to_y = tile < n_y;
+        const int64_t q = to_y ? tile : tile - n_y;
+        const int x_word = (int)(q % xw);
+        const int64_t r = q / xw;
+        const int rt = (int)(r % (to_y ? ty : tz));      // tile of the transposed coordinate
+        const int plane = (int)(r / (to_y ? ty : tz));    // z for my, y for mz
+        const int row = rt * 32 + lane;                   // y (my) or z (mz) of this lane's row
+        uint32_t wv = 0;
+        if (to_y ? row < g.ny : row < g.nz) {
+            const int64_t rr = to_y ? (int64_t)plane * g.ny + row : (int64_t)row * g.ny + plane;
+            wv = mask[rr * wpr + x_word];
+        }
+        uint32_t mine = 0;
+#pragma unroll
+        for (int cbit = 0; cbit < 32; ++cbit) {
+            const uint32_t col = __ballot_sync(0xffffffffu, (wv >> cbit) & 1u);
+            if (lane == cbit) mine = col;
+        }
+        const int x = x_word * 32 + lane;
+        if (x < g.nx) {
+            if (to_y && my) my[((int64_t)plane * g.nx + x) * wy + rt] = mine;
+            if (!to_y && mz) mz[((int64_t)plane * g.nx + x) * wz + rt] = mine;
         }
     }
 }
@@ -378,27 +437,43 @@ __global__ void k_boundary_pair_f32(GridGeom g, const double *__restrict__ xyz, 
 
 // Zero interior, Dirichlet faces, zero padding: the initial state of a leg (Sec. 2.2).
 template <typename T>
+struct InitVec;
+template <>
+struct InitVec<float> {
+    using type = float4;
+    static constexpr int n = 4;
+};
+template <>
+struct InitVec<double> {
+    using type = double2;
+    static constexpr int n = 2;
+};
+
+// A thread per 16-byte vector of the padded state (rows of pitch elements, pitch a multiple of 32).
+template <typename T>
 __global__ void k_init_leg(GridGeom g, const double *__restrict__ bc, T *__restrict__ u) {
-    const int64_t total = (int64_t)g.nz * g.ny * g.pitch;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(p % g.pitch);
-        const int64_t r = p / g.pitch;
-        const int j = (int)(r % g.ny), k = (int)(r / g.ny);
-        T v = T(0);
-        if (i < g.nx) {
-            const bool face = i == 0 || j == 0 || k == 0 || i == g.nx - 1 || j == g.ny - 1 || k == g.nz - 1;
-            if (face) {
-                const int64_t A = (int64_t)g.nx * g.ny, B = (int64_t)g.nx * (g.nz - 2),
-                              Cc = (int64_t)(g.ny - 2) * (g.nz - 2);
-                int64_t f;
-                if (k == 0 || k == g.nz - 1) f = (k == 0 ? 0 : A) + (int64_t)j * g.nx + i;
-                else if (j == 0 || j == g.ny - 1) f = 2 * A + (j == 0 ? 0 : B) + (int64_t)(k - 1) * g.nx + i;
-                else f = 2 * A + 2 * B + (i == 0 ? 0 : Cc) + (int64_t)(k - 1) * (g.ny - 2) + (j - 1);
-                v = (T)bc[f];
+    using V = typename InitVec<T>::type;
+    constexpr int NV = InitVec<T>::n;
+    const int vpr = g.pitch / NV;
+    const int total = g.nz * g.ny * vpr;  // below 2^31 for every admitted grid
+    const int64_t A = (int64_t)g.nx * g.ny, B = (int64_t)g.nx * (g.nz - 2), Cc = (int64_t)(g.ny - 2) * (g.nz - 2);
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+        const int row = q / vpr, c = q - row * vpr;
+        const int j = row % g.ny, k = row / g.ny;
+        const bool zface = k == 0 || k == g.nz - 1, yface = j == 0 || j == g.ny - 1;
+        alignas(16) T v[NV];
+#pragma unroll
+        for (int e = 0; e < NV; ++e) {
+            const int i = c * NV + e;
+            v[e] = T(0);
+            if (i < g.nx) {
+                if (zface) v[e] = (T)bc[(k == 0 ? 0 : A) + (int64_t)j * g.nx + i];
+                else if (yface) v[e] = (T)bc[2 * A + (j == 0 ? 0 : B) + (int64_t)(k - 1) * g.nx + i];
+                else if (i == 0 || i == g.nx - 1)
+                    v[e] = (T)bc[2 * A + 2 * B + (i == 0 ? 0 : Cc) + (int64_t)(k - 1) * (g.ny - 2) + (j - 1)];
             }
         }
-        u[p] = v;
+        reinterpret_cast<V *>(u)[(int64_t)row * vpr + c] = *reinterpret_cast<const V *>(v);
     }
 }
 
@@ -451,7 +526,12 @@ static inline int blocks_for(int64_t n, int t) { return (int)std::min<int64_t>((
 cudaError_t setup_mask(const GridGeom &g, const double *xyz, const double *radius, int n_atoms,
                        uint32_t *mask, uint32_t *hx, uint32_t *hy, uint32_t *hz, uint32_t *my, uint32_t *mz,
                        cudaStream_t st) {
-    if (n_atoms > 0) k_mask_atoms<<<n_atoms, 256, 0, st>>>(g, xyz, radius, n_atoms, mask, hx, hy, hz, my, mz);
+    if (n_atoms > 0) k_mask_atoms<<<n_atoms, 128, 0, st>>>(g, xyz, radius, n_atoms, mask, hx, hy, hz);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || (!my && !mz)) return e;
+    const int64_t tiles = (int64_t)(((g.nx + 31) >> 5)) * ((int64_t)g.nz * ((g.ny + 31) >> 5) + (int64_t)g.ny * ((g.nz + 31) >> 5));
+    const int blocks = (int)std::min<int64_t>((tiles + 7) / 8, 152 * 16);
+    k_mask_transpose<<<blocks, 256, 0, st>>>(g, mask, my, mz);
     return cudaGetLastError();
 }
 
@@ -493,9 +573,9 @@ cudaError_t setup_boundary_pair(const GridGeom &g, const double *xyz, const doub
 }
 
 cudaError_t init_leg(int prec, const GridGeom &g, const double *bc, void *u, cudaStream_t st) {
-    const int64_t total = (int64_t)g.nz * g.ny * g.pitch;
     const int t = 256;
-    const int b = std::min<int64_t>((total + t - 1) / t, 152 * 16);
+    const int64_t vecs = (int64_t)g.nz * g.ny * g.pitch / (prec == 0 ? 2 : 4);
+    const int b = (int)std::min<int64_t>((vecs + t - 1) / t, 152 * 16);
     if (prec == 0) k_init_leg<double><<<b, t, 0, st>>>(g, bc, (double *)u);
     else k_init_leg<float><<<b, t, 0, st>>>(g, bc, (float *)u);
     return cudaGetLastError();
