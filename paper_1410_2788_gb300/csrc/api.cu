@@ -48,7 +48,7 @@ cudaError_t prepare_sweep_f32();
 cudaError_t prepare_sweep_f64();
 cudaError_t launch_energy(int prec, const void *s_tau, const void *s_half, const void *v_tau,
                           const void *v_half, const int64_t *off, const double *qt, const int32_t *n_ent,
-                          int richardson, const double *vac, double *out, cudaStream_t st);
+                          int richardson, const double *vac, double *part, double *out, cudaStream_t st);
 
 // Shapes the line solver is instantiated for (kept in sync with NPB_SWEEP_SHAPES).
 static const SweepShape kShapes[] = {{16, 2, 17}, {16, 4, 9},   {16, 4, 17}, {16, 8, 9},
@@ -340,7 +340,7 @@ extern "C" size_t npb_grid_footprint(const npb_problem *p, int32_t precision) {
     b += 2 * lines * 4 + raw * (4 + 8 + 8 + 8);                              // charge list
     b += 3 * lines * 4 + 2 * raw * sizeof(RawEntry) + 64;                    // its build scratch
     b += 2 * (size_t)face_count(p->n[0], p->n[1], p->n[2]) * 8;              // face data, 2 media
-    b += na * 5 * 8 + 4 * sizeof(LegDev) + 4096;                             // atoms, legs, result
+    b += na * 5 * 8 + 4 * sizeof(LegDev) + kEnergyScratch * 8 + 4096;        // atoms, legs, energy, result
     return b;
 }
 
@@ -399,6 +399,8 @@ int npb::grid_build(npb_ctx *ctx, const npb_problem *p, cudaStream_t st, npb_gri
     if ((rc = galloc(g, &g->d_ent_off, n_raw))) return guard(rc);
     if ((rc = galloc(g, &g->d_ent_xq, n_raw))) return guard(rc);
     if ((rc = galloc(g, &g->d_result, 8))) return guard(rc);
+    if ((rc = galloc(g, &g->d_epart, kEnergyScratch))) return guard(rc);
+    CU(cudaMemsetAsync(g->d_epart, 0, kEnergyScratch * sizeof(double), st));
     if ((rc = galloc(g, &g->d_err, 4))) return guard(rc);
     CU(cudaMemsetAsync(g->d_err, 0, 4 * sizeof(int32_t), st));
     if ((rc = ctx->pinned_slot(&g->h_result))) return guard(rc);
@@ -838,7 +840,7 @@ int npb::enqueue_energy(npb_grid *g, const npb_opts *o, cudaStream_t st) {
     void *const *U = g->d_u[prec];
     CU(launch_energy(prec, U[kLegSlot[0]], U[kLegSlot[1]], U[kLegSlot[2]], U[kLegSlot[3]],
                      g->d_ent_off, g->d_ent_qt, g->sc.total, re, o->vacuum_recovery ? nullptr : g->d_vac_fft,
-                     g->d_result, st));
+                     g->d_epart, g->d_result, st));
     if ((rc = g->ctx->prof.end(st, ev, K_ENERGY))) return rc;
     CU(cudaMemcpyAsync(g->h_result, g->d_result, sizeof(double), cudaMemcpyDeviceToHost, st));
     CU(cudaMemcpyAsync(reinterpret_cast<int32_t *>(g->h_result + 1), g->d_err, sizeof(int32_t),
@@ -850,7 +852,7 @@ int npb::enqueue_energy(npb_grid *g, const npb_opts *o, cudaStream_t st) {
 int npb::enqueue_energy_reduce(npb_grid *g, int prec, int richardson, cudaStream_t st) {
     void *const *U = g->d_u[prec];
     CU(launch_energy(prec, U[kLegSlot[0]], U[kLegSlot[1]], U[kLegSlot[2]], U[kLegSlot[3]], g->d_ent_off,
-                     g->d_ent_qt, g->sc.total, richardson, nullptr, g->d_result, st));
+                     g->d_ent_qt, g->sc.total, richardson, nullptr, g->d_epart, g->d_result, st));
     CU(cudaMemcpyAsync(g->h_result, g->d_result, sizeof(double), cudaMemcpyDeviceToHost, st));
     CU(cudaMemcpyAsync(reinterpret_cast<int32_t *>(g->h_result + 1), g->d_err, sizeof(int32_t),
                        cudaMemcpyDeviceToHost, st));

@@ -65,6 +65,11 @@ struct AddLeg {
     double q, omq;             // AOS: exp(-4 kbar^2 tau) and 1 - that
 };
 
+// The energy reduction: blocks of a launch, threads per block.  Its scratch is kEnergyBlocks
+// doubles of block partials followed by a 32-bit counter (zero between launches).
+constexpr int kEnergyBlocks = 256, kEnergyThreads = 256;
+constexpr int kEnergyScratch = kEnergyBlocks + 1;  // doubles
+
 // Stage flags for the sweep kernels.
 enum : int {
     FUSE_PRE_SRC = 1,   // X sweep: add tau Q to the loaded line (LODIE2 stage S)

@@ -156,6 +156,7 @@ struct npb_grid {
     int last_richardson = 1;       // flags of the last npb_energy (for the recovered potential)
     int last_vacuum_lod = 1;
     double *d_result = nullptr;
+    double *d_epart = nullptr;   // energy reduction scratch: block partials and a counter
     double *h_result = nullptr;  // pinned
     int32_t *d_err = nullptr;    // set by a device wait that expired
     CUtensorMap tma_u[3][3][4];  // FP32 leg states by [direction][lines-per-tile variant][slot]

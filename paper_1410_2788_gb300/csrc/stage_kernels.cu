@@ -6,8 +6,9 @@
 //   add         u += tau rho over the interior, for a dense source density (Sec. 4.1)
 //   energy      Eqs. (rich) and (deltaG3): the FP64 charge-weighted sum over the
 //               charge nodes of the Richardson-combined solvent minus vacuum potential,
-//               reduced in a fixed order (one block, fixed tree), so the value does not
-//               depend on scheduling.
+//               reduced in a fixed order (each block a fixed chunk of the entries and a fixed
+//               tree; the last block to finish sums the block partials in a fixed tree), so the
+//               value does not depend on scheduling.
 #include <algorithm>
 
 #include "npb_internal.cuh"
@@ -250,11 +251,14 @@ __global__ void k_energy(const T *__restrict__ s_tau, const T *__restrict__ s_ha
                          const T *__restrict__ v_tau, const T *__restrict__ v_half,
                          const int64_t *__restrict__ off, const double *__restrict__ qt,
                          const int32_t *__restrict__ n_ent_dev, int richardson, const double *__restrict__ vac,
-                         double *__restrict__ out) {
-    __shared__ double part[1024];
+                         double *__restrict__ part, unsigned int *__restrict__ done, double *__restrict__ out) {
+    __shared__ double red[kEnergyThreads];
+    __shared__ bool last;
     const int n_ent = *n_ent_dev;
+    const int chunk = (n_ent + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int e0 = blockIdx.x * chunk, e1 = min(n_ent, e0 + chunk);
     double acc = 0.0;
-    for (int e = threadIdx.x; e < n_ent; e += blockDim.x) {
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
         const int64_t p = off[e];
         double us, uv;
         if (richardson) {
@@ -267,26 +271,45 @@ __global__ void k_energy(const T *__restrict__ s_tau, const T *__restrict__ s_ha
         if (vac) uv = vac[p];  // Eq. (deltaG2): phi_0^FFT in place of the vacuum legs
         acc += qt[e] * (us - uv);
     }
-    part[threadIdx.x] = acc;
+    red[threadIdx.x] = acc;
     __syncthreads();
     for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) part[threadIdx.x] += part[threadIdx.x + s];
+        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
         __syncthreads();
     }
-    if (threadIdx.x == 0) *out = 0.5 * kKT * part[0];
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = red[0];
+        __threadfence();
+        last = atomicAdd(done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    // the block that finished last sums the block partials, in the same tree whichever block it is
+    __threadfence();
+    red[threadIdx.x] = (int)threadIdx.x < (int)gridDim.x ? reinterpret_cast<volatile double *>(part)[threadIdx.x] : 0.0;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        *out = 0.5 * kKT * red[0];
+        *done = 0u;  // ready for the next launch
+    }
 }
 
 cudaError_t launch_energy(int prec, const void *s_tau, const void *s_half, const void *v_tau,
                           const void *v_half, const int64_t *off, const double *qt, const int32_t *n_ent,
-                          int richardson, const double *vac, double *out, cudaStream_t st) {
+                          int richardson, const double *vac, double *part, double *out, cudaStream_t st) {
+    unsigned int *done = reinterpret_cast<unsigned int *>(part + kEnergyBlocks);
     if (prec == 0)
-        k_energy<double><<<1, 1024, 0, st>>>((const double *)s_tau, (const double *)s_half,
-                                             (const double *)v_tau, (const double *)v_half, off, qt,
-                                             n_ent, richardson, vac, out);
+        k_energy<double><<<kEnergyBlocks, kEnergyThreads, 0, st>>>((const double *)s_tau, (const double *)s_half,
+                                                                   (const double *)v_tau, (const double *)v_half,
+                                                                   off, qt, n_ent, richardson, vac, part, done, out);
     else
-        k_energy<float><<<1, 1024, 0, st>>>((const float *)s_tau, (const float *)s_half,
-                                            (const float *)v_tau, (const float *)v_half, off, qt, n_ent,
-                                            richardson, vac, out);
+        k_energy<float><<<kEnergyBlocks, kEnergyThreads, 0, st>>>((const float *)s_tau, (const float *)s_half,
+                                                                  (const float *)v_tau, (const float *)v_half, off,
+                                                                  qt, n_ent, richardson, vac, part, done, out);
     return cudaGetLastError();
 }
 
