@@ -591,3 +591,20 @@ def test_additive_step_equals_dense_solve(oracle_lib, scheme):
     ref = u.copy()
     ref[inner] = ((w + sum(parts)) / 4 if aos else sum(parts) / 3)[inner]
     assert np.allclose(got, ref, rtol=1e-11, atol=1e-11), np.max(np.abs(got - ref))
+
+
+@pytest.mark.parametrize("scheme", [4, 5, 6, 7, 8, 9, 10])
+def test_first_order_in_time_other_schemes(oracle_lib, scheme):
+    """The remarks of Sec. 3.1-3.3: LODCN, AOS and MAOS are first order in time as well.  Successive
+    halvings of dt at fixed T shrink the change by a factor close to 2 (the implicit-Euler AOS schemes
+    reach it more slowly: 1.59 from dt = 0.02, 1.75 from dt = 0.01)."""
+    us = [sphere_case.run(0.5, dt=dt, T=2.0, scheme=scheme)[1] for dt in (0.01, 0.005, 0.0025)]
+    ratio = np.linalg.norm(us[0] - us[1]) / np.linalg.norm(us[1] - us[2])
+    assert 1.6 < ratio < 2.6, (scheme, ratio)
+
+
+@pytest.mark.parametrize("H", [1.0, 20.0])
+def test_paper_table1_lodcn_stable_at_dt5(oracle_lib, H):
+    """Table 1, LOD row (the LODCN schemes among them): finite after 1e4 steps of dt = 5."""
+    (l2, _), u = sphere_case.run(0.5, dt=5.0, n_steps=10000, H=H, scheme=4)
+    assert np.all(np.isfinite(u)) and l2 < 10.0, (H, l2)
