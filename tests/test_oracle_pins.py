@@ -608,3 +608,50 @@ def test_paper_table1_lodcn_stable_at_dt5(oracle_lib, H):
     """Table 1, LOD row (the LODCN schemes among them): finite after 1e4 steps of dt = 5."""
     (l2, _), u = sphere_case.run(0.5, dt=5.0, n_steps=10000, H=H, scheme=4)
     assert np.all(np.isfinite(u)) and l2 < 10.0, (H, l2)
+
+
+def test_euler_steady_state_equals_newton_solve(oracle_lib):
+    """The explicit-Euler reference (Sec. 5.2) converges to the steady state of Eq. (TimeDepNPB) on
+    the grid: the root of sum_d delta_d^2 u - kbar^2 sinh u + rho = 0 with the face values as Dirichlet
+    data, found here by Newton's method on the dense system (a tiny grid, random eps at half points,
+    random kbar^2 and rho)."""
+    rng = np.random.default_rng(2024)
+    nz, ny, nx = 5, 6, 7
+    h = 0.5
+    u0 = np.zeros((nz, ny, nx))
+    faces = np.ones(u0.shape, dtype=bool)
+    faces[1:-1, 1:-1, 1:-1] = False
+    u0[faces] = rng.normal(size=faces.sum()) * 0.5
+    e_half = tuple(np.ascontiguousarray(rng.uniform(1.0, 4.0, size=u0.shape)) for _ in range(3))
+    k2 = np.where(rng.random(u0.shape) < 0.6, rng.uniform(0.2, 1.5, size=u0.shape), 0.0)
+    rho = rng.normal(size=u0.shape)
+    st = oracle_lib.Setup(np.zeros(u0.shape, np.uint8), None, np.ascontiguousarray(rho), np.ones(u0.shape),
+                          np.ascontiguousarray(k2), e_half, u0.copy())
+    # explicit Euler to its steady state (tau within the stability bound h^2 / (6 max eps))
+    tau = 0.5 * h * h / (6 * 4.0)
+    ue = u0.copy()
+    oracle_lib.euler_run(ue, st, tau, h, 20000)
+    # Newton on the interior unknowns, the operator assembled column by column from _delta2
+    inner = ~faces
+    idx = np.flatnonzero(inner)
+
+    def resid(u):
+        lap = sum(_delta2(u, e_half[d], d, h) for d in range(3))
+        return (lap - k2 * np.sinh(u) + rho).ravel()[idx]
+
+    n = idx.size
+    J0 = np.zeros((n, n))
+    for c in range(n):
+        x = np.zeros(u0.size)
+        x[idx[c]] = 1.0
+        x = x.reshape(u0.shape)
+        J0[:, c] = sum(_delta2(x, e_half[d], d, h) for d in range(3)).ravel()[idx]
+    un = u0.copy()
+    for _ in range(30):
+        J = J0 - np.diag((k2 * np.cosh(un)).ravel()[idx])
+        step = np.linalg.solve(J, -resid(un))
+        un.ravel()[idx] += step
+        if np.max(np.abs(step)) < 1e-14:
+            break
+    assert np.max(np.abs(resid(un))) < 1e-10
+    assert np.max(np.abs(ue - un)) < 1e-9 * max(1.0, np.max(np.abs(un))), np.max(np.abs(ue - un))
