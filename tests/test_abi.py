@@ -72,3 +72,16 @@ def test_no_device_is_reported_not_crashed(lib):
     with pytest.raises(npb.NpbError):
         npb.npb_ctx_create(0, 0)
     assert npb.npb_version().startswith("npb-lod-gb300")
+
+
+def test_binding_constants_match_header():
+    """Every NPB_* integer constant the header defines has the same value in the binding."""
+    import paper_1410_2788_gb300 as npb
+
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    defs = dict(re.findall(r"^#define\s+(NPB_\w+)\s+\(?(-?\d+)\)?\s*$", text, flags=re.M))
+    assert len(defs) > 30
+    missing = [k for k in defs if not hasattr(npb, k)]
+    assert not missing, missing
+    wrong = {k: (getattr(npb, k), int(v)) for k, v in defs.items() if getattr(npb, k) != int(v)}
+    assert not wrong, wrong
