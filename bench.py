@@ -56,6 +56,15 @@ def point_steps(problem, n: int) -> int:
     return (nx - 2) * (ny - 2) * (nz - 2) * n * 6  # (n + 2n) steps x 2 media
 
 
+def workload_config(args, problem, w) -> dict:
+    """The workload part of the JSON line's config, the same for both arms."""
+    nx, ny, nz = problem.n
+    return {"workload": f"{args.workload} (LODIE2 RE+V, {nx}x{ny}x{nz}, {problem.n_atoms} atoms, "
+                        f"dt={w['dt']}, alpha={w['alpha']:.4g}, {w['n']}+{2 * w['n']} steps x 2 media)",
+            "grid": [nx, ny, nz], "atoms": problem.n_atoms, "energy_dtype": "f64",
+            "point_steps_per_step": point_steps(problem, w["n"])}
+
+
 # ----------------------------------------------------------------------------- distributed
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -190,7 +199,9 @@ def run_reference(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": args.workload},
+            "config": dict(workload_config(args, problem, w), l2="host run (no device cache)",
+                           step="one RE+V solve of the oracle (a bounded sample for large_20k)",
+                           parallelism=f"{cores} host threads"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -548,12 +559,9 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == npb.NPB_FP32_SWEEP else "f64",
         "data": "synthetic",
-        "config": {"workload": f"{args.workload} (LODIE2 RE+V, {nx}x{ny}x{nz}, {problem.n_atoms} atoms, "
-                               f"dt={w['dt']}, alpha={w['alpha']:.4g}, {w['n']}+{2 * w['n']} steps x 2 media)",
-                   "grid": [nx, ny, nz], "atoms": problem.n_atoms, "energy_dtype": "f64",
-                   "point_steps_per_step": units_per_step, "l2": "flushed (256 MB write) before every step",
-                   "step": "set-up kernels + 4 legs + FP64 energy + 8-byte read-back",
-                   "parallelism": f"replicas x{world}"},
+        "config": dict(workload_config(args, problem, w), l2="flushed (256 MB write) before every step",
+                       step="set-up kernels + 4 legs + FP64 energy + 8-byte read-back",
+                       parallelism=f"replicas x{world}"),
         "dG_kcal_mol": dg,
         "solves_per_s": args.steps * world / total_s,
         "fp64_path": {"value": u64 / t64 / 1e6, "unit": UNIT, "ms_per_step": 1e3 * t64 / k64,
