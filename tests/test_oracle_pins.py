@@ -713,3 +713,124 @@ def test_vacuum_fft_tends_to_coulomb(oracle_lib):
         ref = C * 1.0 / (2.0 * r[sel])
         errs.append(float(np.max(np.abs(u[sel] - ref) / ref)))
     assert errs[0] < 0.025 and errs[1] < 0.3 * errs[0], errs
+
+
+# --------------------------------------------------------------------------- Eq. (deltaG2) energy
+def _direct_steady_state(oracle_lib, p, medium):
+    """The unsplit discrete steady state of Eq. (TimeDepNPB) at kbar = 0: the linear system
+    -sum_d delta_d(e delta_d u) = rho on the interior nodes, e at half points as the set-up gives it,
+    the Dirichlet faces moved to the right-hand side, solved by conjugate gradients to 1e-14 (the
+    matrix is symmetric positive definite).  Written here from the stencil of Eq. (SpatialOperators),
+    independently of the oracle's line solves."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spl
+
+    st = oracle_lib.setup(p, medium)
+    u0, h2 = st.u0, p.h * p.h
+    inner = np.zeros(u0.shape, dtype=bool)
+    inner[1:-1, 1:-1, 1:-1] = True
+    idx = -np.ones(u0.shape, dtype=np.int64)
+    n_in = int(inner.sum())
+    idx[inner] = np.arange(n_in)
+    node = np.nonzero(inner)
+    b = st.rho[inner].copy()
+    diag = np.zeros(n_in)
+    rows, cols, vals = [], [], []
+    for axis, e in zip((2, 1, 0), st.e_half):  # e_half[d] sits between node and node + 1 along d
+        for step in (1, -1):
+            lo = [c.copy() for c in node]
+            if step == -1:
+                lo[axis] -= 1
+            w = e[tuple(lo)] / h2
+            nb = [c.copy() for c in node]
+            nb[axis] += step
+            j = idx[tuple(nb)]
+            diag += w
+            inside = j >= 0
+            rows.append(np.nonzero(inside)[0])
+            cols.append(j[inside])
+            vals.append(-w[inside])
+            b[~inside] += w[~inside] * u0[tuple(c[~inside] for c in nb)]
+    A = sp.csr_matrix((np.concatenate(vals + [diag]), (np.concatenate(rows + [np.arange(n_in)]),
+                                                         np.concatenate(cols + [np.arange(n_in)]))),
+                      shape=(n_in, n_in))
+    x, info = spl.cg(A, b, rtol=1e-14, maxiter=50000)
+    assert info == 0
+    u = u0.copy()
+    u[inner] = x
+    return u, st
+
+
+def test_energy_fft_tends_to_direct_discrete_energy(oracle_lib):
+    """Eq. (deltaG2) (`energy_fft`): the LOD solvent potential against phi_0^FFT.  On the Born ion
+    (kbar = 0) it must tend, as tau -> 0, to the energy of the unsplit discrete steady state against
+    the vacuum Poisson solution, both solved directly here; with Richardson extrapolation (Eq. rich)
+    the splitting error falls as tau^2, without it as tau (Sec. 3.1 remark).  That limit in turn
+    approaches the Born closed form -81.98 kcal/mol at first order in h (4.2% at h = 0.5, 1.7% at
+    h = 0.25).  A sign slip, a dropped Richardson term or a wrong vacuum potential fails one of
+    these."""
+    ref = _born_closed_form(1.0, 2.0, 1.0, 80.0)
+    limits = []
+    for n, h in [(33, 0.5), (65, 0.25)]:
+        p = I.born_sphere(0.0, n=n, h=h)
+        us, st = _direct_steady_state(oracle_lib, p, oracle_lib.SOLVENT)
+        uv, _ = _direct_steady_state(oracle_lib, p, oracle_lib.VACUUM)
+        assert np.max(np.abs(oracle_lib.vacuum_fft(p) - uv)) <= 1e-11 * np.max(np.abs(uv))
+        limits.append(0.5 * 0.592183 * float(np.sum(st.qt * (us - uv))))
+    errs = [abs(d - ref) / abs(ref) for d in limits]
+    assert errs[0] < 0.05 and errs[1] < 0.02 and errs[0] / errs[1] > 2.0, (limits, errs)
+    # tau -> 0 at h = 0.5, pseudo-time T = 20 (the solvent legs are at steady state by then)
+    p = I.born_sphere(0.0, n=33, h=0.5)
+    re, plain = [], []
+    for tau in (0.02, 0.01, 0.005):
+        n = int(round(20.0 / tau))
+        re.append(oracle_lib.energy_fft(p, tau, n) - limits[0])
+        plain.append(oracle_lib.energy_fft(p, tau, n, richardson=False) - limits[0])
+    for a, b in zip(plain, plain[1:]):
+        assert 1.8 < a / b < 2.2, plain
+    for a, b in zip(re, re[1:]):
+        assert 3.3 < a / b < 4.4, re
+    assert abs(re[-1]) < 0.005 * abs(limits[0])
+
+
+# --------------------------------------------------------------------------- midpoint eps (Sec. 3.1)
+def test_eps_half_midpoint_is_a_lattice_count(oracle_lib):
+    """The midpoint reading of eps at half points: for one atom on a node, the half point
+    (i + 1/2, j, k) (in units of h from the atom, and likewise along y and z) is inside exactly
+    when (2i + 1)^2 + (2j)^2 + (2k)^2 <= (2R/h)^2, an integer test.  Solvent legs take eps_in
+    there and eps_out elsewhere; vacuum legs eps_in everywhere; the last half-point layer along
+    each direction lies outside the grid and is zero."""
+    p = I.born_sphere(0.0, n=17, h=0.5, radius=2.0, eps_in=2.0, eps_out=80.0)
+    c = 8
+    k, j, i = np.meshgrid(*(np.arange(17) - c,) * 3, indexing="ij")
+    offs = [(2 * i + 1, 2 * j, 2 * k), (2 * i, 2 * j + 1, 2 * k), (2 * i, 2 * j, 2 * k + 1)]
+    solvent = oracle_lib.eps_half_midpoint(p, oracle_lib.SOLVENT)
+    vacuum = oracle_lib.eps_half_midpoint(p, oracle_lib.VACUUM)
+    for d in range(3):
+        a, b, cc = offs[d]
+        inside = a * a + b * b + cc * cc <= 64  # (2R/h)^2 = 8^2
+        ref = np.where(inside, 2.0, 80.0)
+        last = [slice(None)] * 3
+        last[2 - d] = -1
+        ref[tuple(last)] = 0.0
+        assert np.array_equal(solvent[d], ref), d
+        vref = np.full(ref.shape, 2.0)
+        vref[tuple(last)] = 0.0
+        assert np.array_equal(vacuum[d], vref), d
+        assert int(inside[tuple(slice(0, -1) if ax == 2 - d else slice(None) for ax in range(3))].sum()) > 0
+
+
+def test_eps_half_midpoint_equals_sphere_benchmark_construction(oracle_lib):
+    """On the Sec. 4.1 sphere (R = 1 at the centre of [-3, 3]^3) the molecule-based midpoint eps
+    equals the sphere benchmark's own half-point construction (the one that reproduces Table 2),
+    for h = 0.5 and 0.25."""
+    for h in (0.5, 0.25):
+        st, _, _ = sphere_case.build(h, eps_mode="midpoint")
+        n = int(round(6.0 / h)) + 1
+        p = I.Problem(xyz=np.zeros((1, 3)), q=np.array([1.0]), radius=np.array([1.0]), eps_in=1.0,
+                      eps_out=80.0, kappa2=1.0, h=h, n=(n, n, n), origin=(-3.0, -3.0, -3.0))
+        got = oracle_lib.eps_half_midpoint(p, oracle_lib.SOLVENT)
+        for d in range(3):
+            keep = [slice(None)] * 3
+            keep[2 - d] = slice(0, -1)
+            assert np.array_equal(got[d][tuple(keep)], st.e_half[d][tuple(keep)]), (h, d)
