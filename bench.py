@@ -1,18 +1,23 @@
 #!/usr/bin/env python
 """Throughput of the LODIE2 RE+V solve on GB300 (LOD Mpoint-steps/s).
 
-Workload (default): the 1,000-atom random-walk molecule on a 129^3 grid at h = 0.5 A,
-eps 1/80, kbar^2 = 0.84 A^-2, LODIE2 with dt = 0.4, alpha = 1/25, 25 steps, Richardson
-extrapolation (dt/2 leg: 50 steps) and the LOD vacuum legs: 127^3 x 150 interior
-point-steps per solve.  Sweeps in FP32, combination and energy in FP64; the plain
-FP64 path is timed beside it.
+Workload (default): the largest single solve, the 20,000-atom random-walk molecule on a 257^3 grid
+at h = 0.5 A, eps 1/80, kbar^2 = 0.84 A^-2, LODIE2 with dt = 0.4, alpha = 1/25, 40 steps,
+Richardson extrapolation (dt/2 leg: 80 steps) and the LOD vacuum legs: 255^3 x 240 interior
+point-steps per solve.  Sweeps in FP32, combination and energy in FP64; the plain FP64 path is
+timed beside it, and both are compared with the FP64 oracle on the same molecule.
 
-One "step" is one complete solve of that molecule with its atoms resident in HBM: the
-set-up kernels (mask, charge list, face data), the four legs, and the energy reduction
-with its 8-byte read-back.  Steps are timed with CUDA events on the solver's stream;
-L2 is flushed (a 256 MB write) before every step, outside the event pair.
+One "step" is one complete solve of that molecule with its atoms resident in HBM: the set-up
+kernels (mask, charge list, face data), the four legs, and the energy reduction with its 8-byte
+read-back.  Steps are timed with CUDA events on the solver's stream; the four leg states (4 x 68
+MB) exceed L2, and a 256 MB write precedes every step, outside the event pair.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Beside the headline: the sweep roofline (each direction's launches timed as the solve issues
+them), the protein_1k configuration (129^3), the batched workload (64 molecules), the Poisson
+serving stream against the plain FP64 path served FIFO, end-to-end timing from pinned host
+arrays, and the oracle on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload W]
 Under torchrun (N > 1) every rank solves its own copy (weak scaling, no collective on
 the data path); rank 0 prints the line with the max over ranks.
 """
@@ -210,39 +215,45 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- our arm
-def cpu_baseline(problem, w, budget_s: float = 12.0):
+def cpu_baseline(problem, w, full_solve_s: float | None = None, budget_s: float = 12.0):
+    """The oracle (plain FP64 C, OpenMP over lines) on the host cores: all cores on the full RE+V
+    solve when `full_solve_s` (its time, set-up included) is given, else on a bounded sample of
+    it; and one thread on one LOD step of the solvent leg (set-up excluded)."""
     import oracle
 
     oracle.build()
     oracle.set_threads(os.cpu_count() or 1)
-    n = w["n"]
-    # a bounded sample: the full RE+V solve, or fewer steps if one solve would run too long
-    nx, ny, nz = problem.n
-    est_rate = 8e7 * oracle.get_threads()  # conservative oracle point-steps/s
-    n_s = n
-    while n_s > 1 and point_steps(problem, n_s) / est_rate > budget_s:
-        n_s = max(1, n_s // 2)
-    t0 = time.perf_counter()
-    reps = 0
-    while True:
-        oracle.energy(problem, w["dt"] / w["alpha"], n_s)
-        reps += 1
-        el = time.perf_counter() - t0
-        if el > budget_s / 2 or reps >= 3:
-            break
-    value = point_steps(problem, n_s) * reps / el / 1e6
-    # one thread on a smaller sample (a single RE+V solve with fewer steps)
     cores = oracle.get_threads()
+    n = w["n"]
+    if full_solve_s is not None:
+        n_s, reps, el = n, 1, full_solve_s
+    else:
+        est_rate = 8e7 * cores  # conservative oracle point-steps/s
+        n_s = n
+        while n_s > 1 and point_steps(problem, n_s) / est_rate > budget_s:
+            n_s = max(1, n_s // 2)
+        t0 = time.perf_counter()
+        reps = 0
+        while True:
+            oracle.energy(problem, w["dt"] / w["alpha"], n_s)
+            reps += 1
+            el = time.perf_counter() - t0
+            if el > budget_s / 2 or reps >= 3:
+                break
+    value = point_steps(problem, n_s) * reps / el / 1e6
+    st = oracle.setup(problem, oracle.SOLVENT)
+    u = st.u0.copy()
     oracle.set_threads(1)
-    n_1 = max(1, n_s // 8)
     t1 = time.perf_counter()
-    oracle.energy(problem, w["dt"] / w["alpha"], n_1)
-    single = point_steps(problem, n_1) / (time.perf_counter() - t1) / 1e6
+    oracle.lod_run(u, st, w["dt"] / w["alpha"], problem.h, 1)
+    t1 = time.perf_counter() - t1
     oracle.set_threads(cores)
+    nx, ny, nz = problem.n
+    single = (nx - 2) * (ny - 2) * (nz - 2) / t1 / 1e6
     return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{reps} RE+V solve(s) of the same molecule with {n_s} steps per dt leg",
+            "sample": f"{reps} full RE+V solve(s) of the same molecule with {n_s} steps per dt leg, set-up included",
             "single_thread": {"value": single, "unit": UNIT,
-                              "sample": f"1 RE+V solve with {n_1} steps per dt leg"},
+                              "sample": "1 LOD step of the solvent leg on 1 thread, set-up excluded"},
             "cpu_model": cpu_model()}
 
 
@@ -261,7 +272,7 @@ def cpu_model() -> str:
     return f"{platform.machine()} implementer {imp[0] if imp else '?'} part {part[0] if part else '?'}"
 
 
-def batch_run(npb, count: int, reps: int = 3):
+def batch_run(npb, count: int, reps: int = 3, tune: bool = True):
     """The batched workload: `count` seeded random-walk molecules of 200-5,000 atoms (log-uniform),
     grids 65^3-161^3 by the grid-size rule, RE+V with FP32 sweeps and FP64 energies.  Times
     npb_energy_batch (equal-size grids share persistent launches; one CUDA graph per batch) against
@@ -280,6 +291,13 @@ def batch_run(npb, count: int, reps: int = 3):
         grids = [npb.npb_grid_create(ctx, p) for p in mols]
         o32 = npb.make_opts(DT, ALPHA, NSTEPS, precision=npb.NPB_FP32_SWEEP)
         pts = sum((p.n[0] - 2) * (p.n[1] - 2) * (p.n[2] - 2) for p in mols) * 6 * NSTEPS
+        # the autotuner picks the line solver per (direction, grid size) on one grid of each size
+        tuned = {}
+        for p, g in zip(mols, grids):
+            if tune and p.n[0] not in tuned:
+                npb.npb_autotune(g, o32, reps=3)
+                tuned[p.n[0]] = {("x", "y", "z")[d]: npb.npb_tune_get(ctx, npb.NPB_FP32_SWEEP, d, p.n[d])
+                                 for d in range(3)}
 
         def timed(fn):
             ms = []
@@ -309,10 +327,12 @@ def batch_run(npb, count: int, reps: int = 3):
             "solves_per_s": count / t_batch * 1e3, "ms_one_at_a_time": t_seq,
             "one_at_a_time_Mpoint_steps_per_s": pts / t_seq / 1e3,
             "same_results": bool(out_b[-1] == out_s[-1]),
+            "tuned_shapes": {str(k): v for k, v in tuned.items()},
+            "alg_gbs": 24 * pts / t_batch / 1e6, "frac_of_peak": 24 * pts / t_batch / 1e6 / measured_peaks()[0],
             "note": "median of %d calls; equal-size grids share one launch per direction per step" % reps}
 
 
-def serving_run(npb, seconds: float, rate: float = 50.0, fifo_requests: int = 12):
+def serving_run(npb, seconds: float, rate: float = 50.0, fifo_requests: int = 50):
     """Poisson arrivals (seeded stream of random-walk molecules, 100-20,000 atoms, h 0.25/0.5 A)
     through npb_submit/npb_poll with continuous batching, FP32 sweeps; then the first
     `fifo_requests` of the same stream through the plain FP64 single-solve path, one at a time
@@ -355,7 +375,7 @@ def serving_run(npb, seconds: float, rate: float = 50.0, fifo_requests: int = 12
     k = min(fifo_requests, count)
     o64 = npb.make_opts(DT, ALPHA, NSTEPS, precision=npb.NPB_FP64)
     ctx = npb.npb_ctx_create(0, 0)
-    lat64 = []
+    lat64, dg64 = [], []
     tf = time.perf_counter()
     for i in range(k):
         ta, p = stream[i]
@@ -363,20 +383,27 @@ def serving_run(npb, seconds: float, rate: float = 50.0, fifo_requests: int = 12
         if now < ta:
             time.sleep(ta - now)
         g = npb.npb_grid_create(ctx, p)
-        npb.npb_energy(g, o64)
+        dg64.append(npb.npb_energy(g, o64))
         npb.npb_grid_destroy(g)
         lat64.append((time.perf_counter() - tf - ta) * 1e3)
     el64 = time.perf_counter() - tf
     npb.npb_ctx_destroy(ctx)
     out["fp64_fifo"] = {"requests": k, "solves_per_s": k / el64, "p50_ms": float(np.percentile(lat64, 50)),
                         "p99_ms": float(np.percentile(lat64, 99)),
-                        "note": "plain FP64 single-solve path, one request at a time in arrival order"}
+                        "note": "plain FP64 single-solve path, one request at a time in arrival order, "
+                                "the first %d requests of the same stream at their arrival times" % k}
+    # each served FP32-sweep result against the FP64 path's (which equals the oracle to 1e-10)
+    rel = [abs(res[i].dG_kcal_mol - dg64[i]) / abs(dg64[i]) for i in range(k)
+           if res[i].status == npb.NPB_OK and dg64[i] != 0.0]
+    out["dG_rel_error_fp32_vs_fp64"] = {"requests": len(rel), "max": max(rel) if rel else None,
+                                        "median": float(np.median(rel)) if rel else None,
+                                        "per_request": [float("%.3g" % r) for r in rel]}
     return out
 
 
 def _kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("sweep_kernel.cuh", "sweep_tma.cuh", "sweep_inner.cuh", "sweep_inner_launch.cuh"):
+    for f in ("sweep_kernel.cuh", "sweep_tma.cuh", "sweep_inner.cuh", "sweep_inner_launch.cuh", "sweep_line.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1410_2788_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -399,6 +426,66 @@ def roofline_traffic(kernel: str, workload: str):
     if not e or e.get("source_hash") != _kernel_source_hash():
         return None
     return e.get("dram_bytes_per_launch")
+
+
+def sweep_roofline(npb, grid, opts, problem, w, elem, peak, peak_kind, workload_name):
+    """The dominant sweep kernel against the HBM roofline, timed the way the solve runs it: each
+    direction's 4-leg and 2-leg launches as graph-captured back-to-back launches (CUDA events on
+    the solver's stream), with the solve's shapes and fused stages.  Per 4-leg launch the
+    algorithmic bytes are 2 * elem * (interior nodes) * 4 legs (read + write of every interior
+    node of every leg); the mask (1/8 B per node) and the charge entries are left out."""
+    nx, ny, nz = problem.n
+    interior = (nx - 2) * (ny - 2) * (nz - 2)
+    names = ("sweep_x", "sweep_y", "sweep_z")
+    t = {}
+    for d in range(3):
+        t[names[d]] = {4: npb.npb_sweep_time(grid, opts, d, 4), 2: npb.npb_sweep_time(grid, opts, d, 2)}
+    n = w["n"]
+    per_step = {k: n * (v[4] + v[2]) for k, v in t.items()}  # ms of each direction in one solve
+    dom = max(per_step, key=per_step.get)
+    alg4 = 2 * elem * interior * 4
+    ms4 = t[dom][4]
+    achieved = alg4 / (ms4 * 1e-3) / 1e9
+    per_dir = {k: {"ms_4_legs": v[4], "ms_2_legs": v[2],
+                   "achieved_gbs_4_legs": alg4 / (v[4] * 1e-3) / 1e9,
+                   "frac_4_legs": alg4 / (v[4] * 1e-3) / 1e9 / peak} for k, v in t.items()}
+    return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": peak_kind,
+            "traffic": roofline_traffic(dom, workload_name),
+            "launch": f"4 legs x {nx - 2}x{ny - 2}x{nz - 2} interior nodes, {alg4 / 1e6:.1f} MB algorithmic",
+            "avg_launch_ms": ms4,
+            "timing": "graph of 8 back-to-back launches replayed 5x, CUDA events on the solver stream",
+            "per_direction": per_dir, "sweeps_ms_per_solve": sum(per_step.values())}
+
+
+def fp32_errors(npb, grid, problem, shape):
+    """The FP32-sweep legs of the last solve, read back for the comparison with the oracle."""
+    return {leg: npb.npb_potential(grid, leg, shape) for leg in range(4)}
+
+
+def error_report(legs32, dg32, dg64, problem, w):
+    """FP32-sweep path and plain FP64 path against the FP64 oracle on the same molecule: the oracle
+    solve of the CPU baseline (full RE+V), its dG and its four legs."""
+    import numpy as np
+
+    import oracle
+
+    oracle.build()
+    oracle.set_threads(os.cpu_count() or 1)
+    t0 = time.perf_counter()
+    ref_dg, ref_legs, st = oracle.energy(problem, w["dt"] / w["alpha"], w["n"], return_legs=True)
+    el = time.perf_counter() - t0
+    names = {0: "solvent_tau", 1: "solvent_half", 2: "vacuum_tau", 3: "vacuum_half"}
+    rep = {"dG_oracle": ref_dg, "dG_fp32_rel": abs(dg32 - ref_dg) / abs(ref_dg),
+           "dG_fp64_rel": abs(dg64 - ref_dg) / abs(ref_dg), "legs": {}}
+    charge = st.qt != 0
+    for leg, got in legs32.items():
+        ref = ref_legs[names[leg]]
+        diff = np.abs(got - ref)
+        rep["legs"][names[leg]] = {"linf_rel": float(diff.max() / np.abs(ref).max()),
+                                   "abs_max_at_charge_nodes": float(diff[charge].max()),
+                                   "abs_max_elsewhere": float(diff[~charge].max())}
+    return rep, el, ref_dg
 
 
 def run_ours(args):
@@ -430,6 +517,8 @@ def run_ours(args):
     opts = npb.make_opts(w["dt"], w["alpha"], w["n"], precision=prec)
     opts64 = npb.make_opts(w["dt"], w["alpha"], w["n"], precision=npb.NPB_FP64)
     tuning = npb.npb_autotune(grid, opts, reps=5) if args.autotune else []
+    shapes = {("x", "y", "z")[d]: dict(zip(("kind", "tx", "seg", "len"), npb.npb_tune_get(ctx, prec, d, problem.n[d])))
+              for d in range(3)}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def step(o):
@@ -456,7 +545,7 @@ def run_ours(args):
     with torch.cuda.stream(stream):
         for _ in range(max(args.warmup, 3)):
             step(opts)
-            step(opts64)
+        step(opts64)
     torch.cuda.synchronize()
 
     # ---- headline: K steps of the FP32-sweep path
@@ -474,15 +563,18 @@ def run_ours(args):
     clk = clocks.stop()
     total_s, total_units = aggregate(sum(step_ms) / 1e3, units_per_step * args.steps, world)
     value = total_units / total_s / 1e6
+    ms_per_step = 1e3 * total_s / args.steps
+    want_errors = world == 1 and rank == 0 and args.cpu_baseline
+    legs32 = fp32_errors(npb, grid, problem, npb.grid_shape(problem)) if want_errors else None
 
     # ---- the plain FP64 path on the same molecule
-    k64 = max(3, args.steps // 2)
+    k64 = max(2, min(3, args.steps))
     ms64, dg64 = timed(opts64, k64)
     t64, u64 = aggregate(sum(ms64) / 1e3, units_per_step * k64, world)
 
-    # ---- per-kernel times (events around every launch, no graph) for the roofline
+    # ---- launches per step and per-kernel shares (events around every launch, no graph)
     npb.npb_ctx_profile(ctx, True)
-    kp = max(2, min(5, args.steps))
+    kp = 2
     with torch.cuda.stream(stream):
         for _ in range(kp):
             flush.zero_()
@@ -492,28 +584,20 @@ def run_ours(args):
     npb.npb_ctx_profile(ctx, False)
     mine = {k: v for k, v in stats.items() if v["launches"] > 0}
     launches_per_step = sum(v["launches"] for v in mine.values()) / kp
-    # the roofline is stated for the sweeps (the hot path); kernel_share lists every kernel
-    sweeps = [k for k in mine if k.startswith("sweep")]
-    dom = max(sweeps or mine, key=lambda k: mine[k]["ms"])
-    nx, ny, nz = problem.n
-    interior = (nx - 2) * (ny - 2) * (nz - 2)
+    share_total = sum(x["ms"] for x in mine.values())
+    kernel_share = {k: round(v["ms"] / share_total, 4) for k, v in mine.items()}
+
+    # ---- roofline of the dominant sweep, timed as the solve launches it
     elem = 4 if prec == npb.NPB_FP32_SWEEP else 8
-    if dom.startswith("sweep"):
-        # per launch: read + write of every interior node of every leg in the launch;
-        # a step launches n sweeps over 4 legs and n over 2 legs
-        bytes_per_step = 2 * elem * interior * (4 * w["n"] + 2 * w["n"])
-        launches = mine[dom]["launches"] / kp
-        alg_per_launch = bytes_per_step / launches
-    else:
-        alg_per_launch = float("nan")
-    avg_ms = mine[dom]["ms"] / mine[dom]["launches"]
-    achieved = alg_per_launch / (avg_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_kind,
-                "traffic": roofline_traffic(dom, args.workload),
-                "alg_bytes_per_launch": alg_per_launch, "avg_launch_ms": avg_ms,
-                "kernel_share": {k: round(v["ms"] / sum(x["ms"] for x in mine.values()), 4) for k, v in mine.items()}}
+    with torch.cuda.stream(stream):
+        roofline = sweep_roofline(npb, grid, opts, problem, w, elem, peak, peak_kind, args.workload)
+    roofline["kernel_share"] = kernel_share
+    roofline["sweeps_share_of_step"] = roofline["sweeps_ms_per_solve"] / ms_per_step
+    alg_step = 2 * elem * 3 * units_per_step  # 3 sweeps x (read + write) per interior point-step
+    roofline["whole_step"] = {"achieved": alg_step / (ms_per_step * 1e-3) / 1e9, "unit": "GB/s",
+                              "frac": alg_step / (ms_per_step * 1e-3) / 1e9 / peak,
+                              "note": "24 B per interior point-step over the whole timed step (set-up included)"}
 
     # ---- end to end through the C ABI from pinned host buffers
     pin = {}
@@ -551,35 +635,111 @@ def run_ours(args):
         if world > 1:
             dist.destroy_process_group()
         return 0
-    base = cpu_baseline(problem, w) if world == 1 else None
-    serving = serving_run(npb, args.serving_seconds) if (world == 1 and args.serving_seconds > 0) else None
-    batch = batch_run(npb, args.batch_count) if (world == 1 and args.batch_count > 0) else None
+    base, errors = None, None
+    if want_errors:
+        errors, el, _ = error_report(legs32, dg, dg64, problem, w)
+        del legs32
+        base = cpu_baseline(problem, w, full_solve_s=el)
+    extra = {}
+    if world == 1 and args.workload != "protein_1k" and args.second_workload:
+        extra["protein_1k"] = second_workload(npb, "protein_1k", prec, args)
+    serving = serving_run(npb, args.serving_seconds, fifo_requests=args.fifo_requests) \
+        if (world == 1 and args.serving_seconds > 0) else None
+    batch = batch_run(npb, args.batch_count, tune=args.autotune) if (world == 1 and args.batch_count > 0) else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == npb.NPB_FP32_SWEEP else "f64",
         "data": "synthetic",
-        "config": dict(workload_config(args, problem, w), l2="flushed (256 MB write) before every step",
+        "config": dict(workload_config(args, problem, w),
+                       l2=("inputs larger than L2 (4 states of %.0f MB), and a 256 MB write before every step"
+                           % (4 * problem.n[0] * problem.n[1] * problem.n[2] * elem / 1e6)),
                        step="set-up kernels + 4 legs + FP64 energy + 8-byte read-back",
                        parallelism=f"replicas x{world}"),
         "dG_kcal_mol": dg,
         "solves_per_s": args.steps * world / total_s,
         "fp64_path": {"value": u64 / t64 / 1e6, "unit": UNIT, "ms_per_step": 1e3 * t64 / k64,
                       "solves_per_s": k64 * world / t64, "dG_kcal_mol": dg64},
+        "error_vs_oracle": errors,
         "wall_s_timed_region": wall,
         "roofline": roofline,
         "cpu_baseline": base,
         "e2e": {"value": ue / te / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8,
                 "call": "npb_grid_create + npb_energy + npb_grid_destroy from pinned host arrays"},
         "gpu_launches": int(round(launches_per_step * args.steps)),
+        "solver_shapes": shapes,
+        "autotune": tuning if args.verbose else sorted(tuning, key=lambda r: (r["dir"], r["ms"]))[:12],
+        "other_workloads": extra,
         "serving": serving,
         "batch": batch,
         "clocks": clk,
-        "autotune": tuning[:0] if not args.verbose else tuning,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+    return 0
+
+
+def second_workload(npb, name, prec, args):
+    """A shorter measurement of another configuration on the same GPU (throughput, sweep roofline)."""
+    import torch
+
+    problem, w = workload(name)
+    units = point_steps(problem, w["n"])
+    stream = torch.cuda.Stream()
+    ctx = npb.npb_ctx_create(0, 0)
+    npb.npb_ctx_set_stream(ctx, stream.cuda_stream)
+    g = npb.npb_grid_create(ctx, problem)
+    o = npb.make_opts(w["dt"], w["alpha"], w["n"], precision=prec)
+    if args.autotune:
+        npb.npb_autotune(g, o, reps=5)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ms = []
+    with torch.cuda.stream(stream):
+        for i in range(3 + args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            npb.npb_grid_refresh(g)
+            npb.npb_energy(g, o)
+            b.record(stream)
+            if i >= 3:
+                ms.append((a, b))
+        torch.cuda.synchronize()
+    t = [x.elapsed_time(y) for x, y in ms]
+    ms_step = sum(t) / len(t)
+    peak, kind = measured_peaks()
+    with torch.cuda.stream(stream):
+        roof = sweep_roofline(npb, g, o, problem, w, 4 if prec == npb.NPB_FP32_SWEEP else 8, peak, kind, name)
+    shapes = {("x", "y", "z")[d]: npb.npb_tune_get(ctx, prec, d, problem.n[d]) for d in range(3)}
+    npb.npb_grid_destroy(g)
+    npb.npb_ctx_destroy(ctx)
+    roof["sweeps_share_of_step"] = roof["sweeps_ms_per_solve"] / ms_step
+    return {"workload": workload_config(args, problem, w)["workload"].replace(args.workload, name),
+            "value": units / (ms_step * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms_step,
+            "solves_per_s": 1e3 / ms_step, "roofline": roof, "solver_shapes": shapes,
+            "l2": "states fit L2 (4 x 8.6 MB); 256 MB write before every step"}
+
+
+def run_once(args):
+    """One RE+V solve of the workload (grid set-up, legs, energy), untimed: the command profilers
+    capture (ncu launch lists and kernel captures), with --once-steps LOD steps per dt leg."""
+    import paper_1410_2788_gb300 as npb
+    from paper_1410_2788_gb300 import build
+
+    build.build()
+    problem, w = workload(args.workload)
+    prec = npb.NPB_FP32_SWEEP if args.precision == "fp32" else npb.NPB_FP64
+    ctx = npb.npb_ctx_create(0, 0)
+    try:
+        g = npb.npb_grid_create(ctx, problem)
+        try:
+            n = args.once_steps if args.once_steps > 0 else w["n"]
+            print("dG", npb.npb_energy(g, npb.make_opts(w["dt"], w["alpha"], n, precision=prec)))
+        finally:
+            npb.npb_grid_destroy(g)
+    finally:
+        npb.npb_ctx_destroy(ctx)
     return 0
 
 
@@ -589,15 +749,26 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="protein_1k", choices=["protein_1k", "large_20k", "born"])
+    ap.add_argument("--workload", default="large_20k", choices=["protein_1k", "large_20k", "born"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--verbose", action="store_true")
     ap.add_argument("--batch-count", type=int, default=64,
                     help="molecules in the batched-workload measurement (0 skips it)")
-    ap.add_argument("--serving-seconds", type=float, default=5.0,
+    ap.add_argument("--serving-seconds", type=float, default=60.0,
                     help="length of the Poisson serving stream measured after the main line (0: skip)")
+    ap.add_argument("--fifo-requests", type=int, default=50,
+                    help="requests of the same stream served by the plain FP64 path, FIFO")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false",
+                    help="skip the oracle timing and the error report against it")
+    ap.add_argument("--no-second-workload", dest="second_workload", action="store_false",
+                    help="skip the protein_1k measurement beside the headline workload")
+    ap.add_argument("--once", action="store_true",
+                    help="run one untimed solve of the workload and exit (for profilers)")
+    ap.add_argument("--once-steps", type=int, default=0, help="LOD steps per dt leg of --once (0: the workload's)")
     args = ap.parse_args(argv)
+    if args.once:
+        return run_once(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

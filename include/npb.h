@@ -164,6 +164,15 @@ int npb_ctx_profile(npb_ctx *ctx, int32_t enable);
  * of classes written.  Synchronises the stream. */
 int npb_ctx_kernel_stats(npb_ctx *ctx, int32_t max_kernels, const char **names,
                          int64_t *launches, double *ms);
+/* Failure-detection probe, to test the error path of the bounded device waits without a GPU
+ * fault.  Every wait of the TMA-pipelined sweeps on their tile copies gives up after about 4e9 SM
+ * cycles (two seconds), sets the grid's error flag and returns; the call reports NPB_ETIMEOUT once
+ * the stream has synchronised, and the context stays usable.  While `cycles` > 0, a probe kernel
+ * runs before every TMA sweep launch: each of its blocks waits, with the same bounded-wait helper
+ * and a bound of `cycles`, on a barrier that nothing arrives at (no copy is in flight), so the wait
+ * expires and sets the same flag.  0 turns the probe off.  Solves run as direct launches (no graph)
+ * while it is on. */
+int npb_ctx_probe_wait_expiry(npb_ctx *ctx, int64_t cycles);
 /* Bytes of device memory the context's grids hold right now. */
 int npb_ctx_memory(npb_ctx *ctx, size_t *in_use, size_t *budget);
 
@@ -242,9 +251,9 @@ int npb_grid_export(npb_grid *grid, int32_t what, void *host_out, size_t n_elems
 
 /* ---- charge list without allocation --------------------------------------------------- */
 /* The paper has no counterpart: this is a service for callers that cannot allocate device
- * memory when they need a charge list -- code in the middle of capturing a CUDA graph,
- * applications whose own memory pool owns the device and forbids library allocations, and
- * latency-critical paths that cannot pay for cudaMalloc's implicit synchronisation.
+ * memory when they need a charge list -- applications whose own memory pool owns the device and
+ * forbids library allocations, and latency-critical paths that cannot pay for the implicit
+ * device synchronisation of cudaMalloc/cudaFree.
  *
  * It builds the same x-line-grouped trilinear charge list as npb_grid_create, on the calling
  * thread's current device and on `stream` (a cudaStream_t; NULL = the legacy default
@@ -252,16 +261,17 @@ int npb_grid_export(npb_grid *grid, int32_t what, void *host_out, size_t n_elems
  * one fixed device array compiled into the library (about 9.3 MB on every GPU that loads it,
  * kept until the process exits), which bounds the problem: n_atoms <= NPB_STATIC_MAX_ATOMS
  * and ny*nz <= NPB_STATIC_MAX_LINES; larger inputs return NPB_EINVAL.  The first call on a
- * device looks the array up (cudaGetSymbolAddress) -- make it before any stream capture.
- * Every call reuses the same array: calls that overlap on the GPU race, so serialise them.
+ * device looks up the array's device address (cudaGetSymbolAddress) with that device current.
+ * Every call reuses the same array and clears what it accumulates into: calls that overlap on
+ * the GPU race, so serialise them.
  *
- * Inputs (host memory): xyz (3*n_atoms doubles), q (n_atoms), grid n, h, origin as in
- * npb_problem; every atom's 8-node stencil must lie in the interior.  Outputs (device memory
- * the caller owns): d_line_begin and d_line_count (ny*nz each; entries of x-line z*ny + y),
- * d_ent_x, d_ent_qt and d_ent_off (room for 8*n_atoms each: node x index, charge in e_c,
- * element offset (z*ny + y)*pitch + x with pitch = nx rounded up to 32), and d_n_entries
+ * Inputs (host memory, read during the call): xyz (3*n_atoms doubles), q (n_atoms), grid n, h,
+ * origin as in npb_problem; every atom's 8-node stencil must lie in the interior.  Outputs
+ * (device memory the caller owns): d_line_begin and d_line_count (ny*nz each; entries of x-line
+ * z*ny + y), d_ent_x, d_ent_qt and d_ent_off (room for 8*n_atoms each: node x index, charge in
+ * e_c, element offset (z*ny + y)*pitch + x with pitch = nx rounded up to 32), and d_n_entries
  * (one int32: the number of entries).  The work is enqueued; synchronise `stream` before
- * reading the outputs. */
+ * reading the outputs.  NPB_ECUDA when a copy, clear or launch is refused. */
 #define NPB_STATIC_MAX_ATOMS 20000
 #define NPB_STATIC_MAX_LINES (288 * 288)
 int npb_charge_list_static(const double *xyz, const double *q, int32_t n_atoms, const int32_t n[3], double h,
@@ -281,33 +291,64 @@ int npb_submit(npb_ctx *ctx, const npb_problem *problem, const npb_opts *opts,
 int npb_poll(npb_ctx *ctx, uint64_t ticket, int32_t timeout_ms, npb_result *out);
 
 /* ---- line-solver autotuning ------------------------------------------------------------ */
-/* Each line of a sweep (the implicit-Euler tridiagonal solve of one LOD direction, Eq. 12)
- * is solved by SEG threads holding L consecutive rows each (a segmented Thomas
- * elimination plus a reduced system over the segment ends), TX lines per thread block.
- * The solver kind selects the kernel family:
- *   NPB_KIND_TILE      0: one tile per block, FP64 or FP32, segments over all n rows,
- *                         reduced system by parallel cyclic reduction;
- *   NPB_KIND_TMA       1: FP32 only, persistent blocks fed by bulk tensor copies, the
- *                         same segmentation as kind 0;
- *   NPB_KIND_TMA_INNER 2: FP32 only, persistent TMA blocks, segments over the n-2 interior
- *                         rows with shared uniform-segment constants and a serial reduced
- *                         solve (the FP32 default).
+/* Each line of a sweep (the implicit-Euler tridiagonal solve of one LOD direction, Eqs. LODIE1_2-4)
+ * is solved by one of four kernel families, the solver kind:
+ *   NPB_KIND_TILE      0: one tile per block, FP64 or FP32: SEG threads per line holding L
+ *                         consecutive rows each (a segmented Thomas elimination), the segment ends
+ *                         reduced by parallel cyclic reduction; TX lines per block.  SEG = 2 is
+ *                         close to Thomas per line, many short segments close to pure PCR;
+ *   NPB_KIND_TMA       1: FP32 only, persistent blocks fed by bulk tensor copies, the same
+ *                         segmentation as kind 0;
+ *   NPB_KIND_TMA_INNER 2: FP32 only, persistent TMA blocks, SEG segments of L rows over the n-2
+ *                         interior rows, segment ends reduced by parallel cyclic reduction in
+ *                         shared memory (x: 8 lines per tile; y/z: 16 or 8);
+ *   NPB_KIND_LINE      3: FP32 only, y and z: the Thomas algorithm of the paper (Sec. 3.1), one
+ *                         line per pair of threads (each eliminates from one end of the line, the
+ *                         two meet in the middle), 32 lines per tile, TMA-pipelined; tx = 32,
+ *                         seg = 2, len = pipeline stages (1 or 2).  Tiles of constant coefficients
+ *                         take the leg's precomputed multipliers.  The FP32 default for y and z.
  * npb_autotune times every instantiated (kind, TX, SEG, L) that covers the grid's lines, on
  * all four legs of `grid` at opts->precision, `reps` launches each, and keeps the fastest
  * per (precision, direction, line length) in the context.  report (may be NULL) receives a
  * JSON list of the timings, truncated to report_len bytes.  The legs' states are
- * overwritten.  Kinds 1 and 2 fall back to kind 0's default shape where the grid's
- * geometry does not suit bulk tensor copies or eps at half points is the midpoint reading. */
-enum { NPB_KIND_TILE = 0, NPB_KIND_TMA = 1, NPB_KIND_TMA_INNER = 2 };
+ * overwritten.  Kinds 1-3 fall back to kind 0's default shape where the grid's geometry does
+ * not suit bulk tensor copies or eps at half points is the midpoint reading; kind 3 falls back
+ * to kind 2 for the Crank-Nicolson and additive schemes. */
+enum { NPB_KIND_TILE = 0, NPB_KIND_TMA = 1, NPB_KIND_TMA_INNER = 2, NPB_KIND_LINE = 3 };
 int npb_autotune(npb_grid *grid, const npb_opts *opts, int32_t reps, char *report, size_t report_len);
 /* Pin / read the shape used for lines of n nodes along dir (0 = x, 1 = y, 2 = z).
  * npb_tune_set fails with NPB_EINVAL when (kind, tx, seg, len) is not instantiated for that
  * precision and direction or covers fewer rows than the kind needs (n, or n - 2 for
- * kind 2).  npb_tune_get returns the pinned shape, else the default for n. */
+ * kind 2; kind 3 covers any line).  npb_tune_get returns the pinned shape, else the default for n. */
 int npb_tune_set(npb_ctx *ctx, int32_t precision, int32_t dir, int32_t n, int32_t kind, int32_t tx,
                  int32_t seg, int32_t len);
 int npb_tune_get(npb_ctx *ctx, int32_t precision, int32_t dir, int32_t n, int32_t *kind, int32_t *tx,
                  int32_t *seg, int32_t *len);
+/* The tuning cache: npb_tune_save writes every shape pinned in the context (by npb_autotune or
+ * npb_tune_set) to the file `path` as a JSON list of {"precision", "dir", "n", "kind", "tx",
+ * "seg", "len"} entries, one per (precision, direction, line length).  npb_tune_load reads such a
+ * file and pins each entry that this build instantiates (others are skipped); *n_loaded (may be
+ * NULL) receives the number pinned.  NPB_EINVAL when the file cannot be written, read or parsed. */
+int npb_tune_save(npb_ctx *ctx, const char *path);
+int npb_tune_load(npb_ctx *ctx, const char *path, int32_t *n_loaded);
+
+/* Average device time (ms) of one sweep launch as npb_energy issues it (measurement aid, not a
+ * stage of the method): direction dir (0 = x, 1 = y, 2 = z) over the legs of slots [0, n_legs)
+ * -- n_legs = 4 is the launch of LOD steps 1 .. n (all four legs of Eq. deltaG3's RE+V solve),
+ * n_legs = 2 the launch of steps n+1 .. 2n (the dt/2 legs) -- with the solve's shape for that
+ * direction and its fused stages (LODIE2: S in the x sweep, N in the z sweep; LODIE1: N in the x
+ * sweep).  reps launches are captured in one CUDA graph on the context stream (which must not be
+ * the legacy default stream), replayed once untimed, then `rounds` times between two CUDA events;
+ * *ms_per_launch = elapsed / (reps * rounds).  The legs' states are overwritten.  Implicit-Euler
+ * LOD schemes only (NPB_EINVAL otherwise). */
+int npb_sweep_time(npb_grid *grid, const npb_opts *opts, int32_t dir, int32_t n_legs, int32_t reps, int32_t rounds,
+                   double *ms_per_launch);
+
+/* Rates of the device's FP64 units (measurement aid for the plain FP64 path's roofline, not a stage
+ * of the method): fused multiply-adds per second and IEEE divisions per second, each from a
+ * kernel of eight independent dependency chains per thread over all SMs, timed with CUDA events on
+ * the context stream after one untimed pass.  Uses 64 bytes of the context's device memory. */
+int npb_measure_fp64(npb_ctx *ctx, double *dfma_per_s, double *ddiv_per_s);
 
 /* ---- errors --------------------------------------------------------------------------- */
 const char *npb_last_error(void);

@@ -76,6 +76,7 @@ SIGNATURES = {
     "npb_ctx_kernel_stats": (_I, [_V, _I32, ctypes.POINTER(ctypes.c_char_p),
                                   ctypes.POINTER(ctypes.c_int64), _dp]),
     "npb_ctx_memory": (_I, [_V, ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)]),
+    "npb_ctx_probe_wait_expiry": (_I, [_V, ctypes.c_int64]),
     "npb_grid_create": (_I, [_V, ctypes.POINTER(npb_problem), ctypes.POINTER(_V)]),
     "npb_grid_destroy": (None, [_V]),
     "npb_grid_refresh": (_I, [_V]),
@@ -92,6 +93,10 @@ SIGNATURES = {
                         ctypes.POINTER(ctypes.c_uint64)]),
     "npb_poll": (_I, [_V, ctypes.c_uint64, _I32, ctypes.POINTER(npb_result)]),
     "npb_autotune": (_I, [_V, ctypes.POINTER(npb_opts), _I32, ctypes.c_char_p, _SZ]),
+    "npb_sweep_time": (_I, [_V, ctypes.POINTER(npb_opts), _I32, _I32, _I32, _I32, _dp]),
+    "npb_measure_fp64": (_I, [_V, _dp, _dp]),
+    "npb_tune_save": (_I, [_V, ctypes.c_char_p]),
+    "npb_tune_load": (_I, [_V, ctypes.c_char_p, ctypes.POINTER(_I32)]),
     "npb_tune_set": (_I, [_V, _I32, _I32, _I32, _I32, _I32, _I32, _I32]),
     "npb_tune_get": (_I, [_V, _I32, _I32, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32),
                           ctypes.POINTER(_I32)]),
@@ -183,6 +188,12 @@ def npb_ctx_kernel_stats(ctx: int) -> dict:
     ms = (ctypes.c_double * n)()
     k = _check(load_library().npb_ctx_kernel_stats(ctx, n, names, launches, ms))
     return {names[i].decode(): {"launches": int(launches[i]), "ms": float(ms[i])} for i in range(k)}
+
+
+def npb_ctx_probe_wait_expiry(ctx: int, cycles: int) -> None:
+    """cycles > 0: a bounded-wait probe that expires after `cycles` SM cycles runs before every TMA
+    sweep launch (testing the NPB_ETIMEOUT path); 0: off."""
+    _check(load_library().npb_ctx_probe_wait_expiry(ctx, int(cycles)))
 
 
 def npb_ctx_memory(ctx: int) -> tuple[int, int]:
@@ -286,7 +297,36 @@ def npb_autotune(grid: int, opts: npb_opts, reps: int = 5) -> list:
     return json.loads(buf.value.decode() or "[]")
 
 
-KIND_TILE, KIND_TMA, KIND_TMA_INNER = 0, 1, 2
+KIND_TILE, KIND_TMA, KIND_TMA_INNER, KIND_LINE = 0, 1, 2, 3
+
+
+def npb_tune_save(ctx: int, path: str) -> None:
+    """Write the context's pinned line-solver shapes to a JSON file."""
+    _check(load_library().npb_tune_save(ctx, os.fsencode(path)))
+
+
+def npb_tune_load(ctx: int, path: str) -> int:
+    """Pin the shapes a JSON tuning file lists; returns how many were pinned."""
+    n = _I32()
+    _check(load_library().npb_tune_load(ctx, os.fsencode(path), ctypes.byref(n)))
+    return n.value
+
+
+def npb_measure_fp64(ctx: int) -> tuple[float, float]:
+    """(FP64 fused multiply-adds per second, FP64 divisions per second) of the context's device."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(load_library().npb_measure_fp64(ctx, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def npb_sweep_time(grid: int, opts: npb_opts, direction: int, n_legs: int = 4, reps: int = 8,
+                   rounds: int = 5) -> float:
+    """Average device ms of one sweep launch along `direction` over n_legs legs, as a solve issues
+    it (graph-captured back-to-back launches, CUDA events on the context stream)."""
+    out = ctypes.c_double()
+    _check(load_library().npb_sweep_time(grid, ctypes.byref(opts), direction, n_legs, reps, rounds,
+                                         ctypes.byref(out)))
+    return out.value
 
 
 def npb_tune_set(ctx: int, precision: int, direction: int, n: int, kind: int, tx: int, seg: int,

@@ -227,6 +227,7 @@ extern "C" int npb_ctx_create(int device, size_t budget, npb_ctx **out) {
     CU(prepare_sweep_f64());
     CU(prepare_sweep_tma());
     CU(prepare_sweep_inner());
+    CU(prepare_sweep_line());
     *out = ctx.release();
     return NPB_OK;
 }
@@ -279,6 +280,13 @@ extern "C" int npb_ctx_kernel_stats(npb_ctx *ctx, int32_t max_kernels, const cha
         if (ms) ms[n] = ctx->prof.total_ms[i];
     }
     return n;
+}
+
+extern "C" int npb_ctx_probe_wait_expiry(npb_ctx *ctx, int64_t cycles) {
+    if (!ctx) return fail(NPB_EINVAL, "ctx is NULL");
+    if (cycles < 0) return fail(NPB_EINVAL, "cycles must be >= 0");
+    ctx->probe_cycles = cycles;
+    return NPB_OK;
 }
 
 extern "C" int npb_ctx_memory(npb_ctx *ctx, size_t *in_use, size_t *budget) {
@@ -474,35 +482,21 @@ extern "C" int npb_grid_create(npb_ctx *ctx, const npb_problem *p, npb_grid **ou
 
 extern "C" void npb_grid_destroy(npb_grid *g) { grid_free(g); }
 
-// Face data of a medium, computed on first use with FP64 (parity path) or FP32 pair
-// terms (mixed path), then cached.
+// Face data of a medium, computed on first use -- both media in one pass, with FP64 pair terms
+// (parity path) or FP32 pair terms (mixed path) -- then cached.
 int npb::grid_boundary(npb_grid *g, int medium, int prec, cudaStream_t st, const double **out) {
     const int kind = prec == NPB_FP64 ? 0 : 1;
     double *&bc = g->d_bc[medium][kind];
-    if (kind == 1 && (!bc || !g->bc_valid[medium][kind])) {  // FP32 pairs: both media in one pass
+    if (!bc || !g->bc_valid[medium][kind]) {
         const int64_t nf = face_count(g->geo.nx, g->geo.ny, g->geo.nz);
         int rc;
         for (int m = 0; m < 2; ++m)
-            if (!g->d_bc[m][1] && (rc = galloc(g, &g->d_bc[m][1], (size_t)nf))) return rc;
-        g->bc_valid[NPB_SOLVENT][1] = g->bc_valid[NPB_VACUUM][1] = true;
+            if (!g->d_bc[m][kind] && (rc = galloc(g, &g->d_bc[m][kind], (size_t)nf))) return rc;
+        g->bc_valid[NPB_SOLVENT][kind] = g->bc_valid[NPB_VACUUM][kind] = true;
         cudaEvent_t ev{};
         if ((rc = g->ctx->prof.begin(st, &ev))) return rc;
         CU(setup_boundary_pair(g->geo, g->d_xyz, g->d_q, g->n_atoms, g->eps_out, std::sqrt(g->kappa2), g->eps_in,
-                               g->d_bc[NPB_SOLVENT][1], g->d_bc[NPB_VACUUM][1], st));
-        if ((rc = g->ctx->prof.end(st, ev, K_SETUP_BOUNDARY))) return rc;
-    }
-    if (!bc || !g->bc_valid[medium][kind]) {
-        int rc;
-        if (!bc) {
-            const int64_t nf = face_count(g->geo.nx, g->geo.ny, g->geo.nz);
-            if ((rc = galloc(g, &bc, (size_t)nf))) return rc;
-        }
-        g->bc_valid[medium][kind] = true;
-        const double eps = medium == NPB_SOLVENT ? g->eps_out : g->eps_in;
-        const double kbar = medium == NPB_SOLVENT ? std::sqrt(g->kappa2) : 0.0;
-        cudaEvent_t ev{};
-        if ((rc = g->ctx->prof.begin(st, &ev))) return rc;
-        CU(setup_boundary(g->geo, g->d_xyz, g->d_q, g->n_atoms, eps, kbar, kind == 1, bc, st));
+                               g->d_bc[NPB_SOLVENT][kind], g->d_bc[NPB_VACUUM][kind], st, kind == 0));
         if ((rc = g->ctx->prof.end(st, ev, K_SETUP_BOUNDARY))) return rc;
     }
     *out = bc;
@@ -541,6 +535,7 @@ int npb::grid_states(npb_grid *g, int prec, cudaStream_t st) {
     }
     int rc = galloc(g, &g->d_legs[prec], 4);
     if (rc) return rc;
+    if (prec == NPB_FP32_SWEEP && (rc = galloc(g, &g->d_line_tab, (size_t)4 * 3 * kLineTabMax))) return rc;
     g->legs_key[prec] = "";
     return 0;
 }
@@ -615,6 +610,23 @@ int npb::grid_prepare(npb_grid *g, const npb_opts *o, cudaStream_t st) {
     snprintf(key, sizeof key, "%.17g/%.17g/%d/%d", o->dt, o->alpha, o->eps_mode, scheme_cn(o->scheme) ? 1 : 0);
     if (g->legs_key[prec] != key) {
         for (int leg = 0; leg < 4; ++leg) g->h_legs[prec][kLegSlot[leg]] = make_leg(g, leg, o);
+        std::vector<float2> tab;
+        if (prec == NPB_FP32_SWEEP && g->d_line_tab) {
+            // per slot and direction: the multipliers of a constant-coefficient line (the leg's r*eps
+            // outside the molecule; vacuum legs carry r*eps_in everywhere)
+            tab.assign((size_t)4 * 3 * kLineTabMax, make_float2(0.f, 0.f));
+            const int n3[3] = {g->geo.nx, g->geo.ny, g->geo.nz};
+            for (int s = 0; s < 4; ++s) {
+                LegDev &L = g->h_legs[prec][s];
+                const double e = L.mask ? L.rE[0] : L.rE[2];
+                for (int d = 0; d < 3; ++d) {
+                    const size_t at = ((size_t)s * 3 + d) * kLineTabMax;
+                    line_table(e, n3[d], tab.data() + at);
+                    L.line_tab[d] = g->d_line_tab + at;
+                }
+            }
+            CU(cudaMemcpyAsync(g->d_line_tab, tab.data(), tab.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
+        }
         CU(cudaMemcpyAsync(g->d_legs[prec], g->h_legs[prec], sizeof(LegDev) * 4, cudaMemcpyHostToDevice, st));
         CU(cudaStreamSynchronize(st));
         g->legs_key[prec] = key;
@@ -629,18 +641,20 @@ SweepShape npb::shape_for(npb_ctx *ctx, int prec, int dir, int n) {
         if (it != ctx->tuned.end()) return it->second;
     }
     if (prec == NPB_FP32_SWEEP) {
-        // interior-row TMA sweeps: rows solved (padding included) plus about eight rows' worth of
-        // work per segment for the reduced system; the cheapest shape covering the n-2 unknowns
-        SweepShape t[32], best{0, 0, 0, 0};
-        const int k = inner_shapes(dir, t, 32);
-        auto cost = [](const SweepShape &s) { return s.seg * s.len + 8 * s.seg; };
-        for (int i = 0; i < k; ++i) {
-            if (t[i].seg * t[i].len < n - 2) continue;
-            if (best.tx == 0 || cost(t[i]) < cost(best)) best = t[i];
-        }
+        // the interior-row segments (the line-per-thread-pair kernel, the paper's plain Thomas,
+        // measured 3x slower on 257^3: latency-bound at the few warps its shared tiles leave room for)
+        const SweepShape best = inner_default_shape(dir, n);
         if (best.tx) return best;
     }
     return default_sweep_shape(prec, dir, n);
+}
+
+// The shape a launch can take for legs that cannot use `s`: the line-per-thread-pair kernel needs
+// every leg's multiplier table and runs the implicit-Euler sweeps only (no fused Crank-Nicolson
+// half step); those legs take the interior-row segments instead.
+SweepShape npb::usable_shape(SweepShape s, int dir, int n, bool tables, int flags) {
+    if (s.kind == 3 && (!tables || (flags & FUSE_PRE_CN))) return inner_default_shape(dir, n);
+    return s;
 }
 
 // Tensor maps of the FP32 leg states and of the mask, built once per grid.
@@ -674,6 +688,9 @@ cudaError_t npb::launch_dir(npb_grid *g, int prec, int d, SweepShape shape, int 
         g->h_legs[prec][slot0].eps_mode == 0) {
         TmaLaunch P;
         memset(&P, 0, sizeof P);
+        bool tables = true;
+        for (int i = 0; i < n_legs; ++i) tables = tables && g->h_legs[prec][slot0 + i].line_tab[d] != nullptr;
+        shape = usable_shape(shape, d, n_dir[d], tables, flags);
         const int v = tma_variant(d, shape.tx);
         if (v < 0) return cudaErrorInvalidValue;
         for (int i = 0; i < n_legs; ++i) {
@@ -683,6 +700,11 @@ cudaError_t npb::launch_dir(npb_grid *g, int prec, int d, SweepShape shape, int 
         }
         P.n_legs = n_legs;
         P.err = g->d_err;
+        if (g->ctx->probe_cycles > 0) {
+            const cudaError_t ep = launch_wait_probe(g->d_err, g->ctx->probe_cycles, g->ctx->sm_count, st);
+            if (ep != cudaSuccess) return ep;
+        }
+        if (shape.kind == 3) return launch_sweep_line(d, P, g->tma_g[d], flags, shape, g->ctx->sm_count, st);
         if (shape.kind == 2) return launch_sweep_inner(d, P, g->tma_g[d], flags, shape, g->ctx->sm_count, st);
         return launch_sweep_tma(d, P, g->tma_g[d], flags, shape, g->ctx->sm_count, st);
     }
@@ -705,8 +727,12 @@ int npb::step_legs(npb_ctx *ctx, const LegRef *refs, int n, const LegDev *d_tabl
     const int n_dir[3] = {nx, ny, nz};
     SweepShape shape[3];
     bool tma[3];
+    const bool cn_scheme = scheme_cn(scheme);
     for (int d = 0; d < 3; ++d) {
         shape[d] = shape_for(ctx, prec, d, n_dir[d]);
+        bool tables = true;
+        for (int i = 0; i < n; ++i) tables = tables && refs[i].g->h_legs[prec][refs[i].slot].line_tab[d] != nullptr;
+        shape[d] = usable_shape(shape[d], d, n_dir[d], tables, cn_scheme ? FUSE_PRE_CN : 0);
         bool ok = shape[d].kind >= 1 && prec == NPB_FP32_SWEEP;
         for (int i = 0; i < n && ok; ++i)
             ok = refs[i].g->tma_ok[d] && refs[i].g->h_legs[prec][refs[i].slot].eps_mode == 0;
@@ -762,7 +788,11 @@ int npb::step_legs(npb_ctx *ctx, const LegRef *refs, int n, const LegDev *d_tabl
                 }
                 P.n_legs = m;
                 P.err = refs[c0].g->d_err;
-                if (shape[d].kind == 2) CU(launch_sweep_inner(d, P, refs[c0].g->tma_g[d], flags, shape[d], ctx->sm_count, st));
+                if (ctx->probe_cycles > 0)
+                    for (int i = 0; i < m; ++i)
+                        CU(launch_wait_probe(refs[c0 + i].g->d_err, ctx->probe_cycles, ctx->sm_count, st));
+                if (shape[d].kind == 3) CU(launch_sweep_line(d, P, refs[c0].g->tma_g[d], flags, shape[d], ctx->sm_count, st));
+                else if (shape[d].kind == 2) CU(launch_sweep_inner(d, P, refs[c0].g->tma_g[d], flags, shape[d], ctx->sm_count, st));
                 else CU(launch_sweep_tma(d, P, refs[c0].g->tma_g[d], flags, shape[d], ctx->sm_count, st));
             }
         } else {
@@ -893,7 +923,7 @@ extern "C" int npb_energy(npb_grid *g, const npb_opts *o, double *dG) {
     if (!o->vacuum_recovery && (rc = grid_vacuum_fft(g, o->precision, st))) return rc;
     g->last_richardson = o->richardson ? 1 : 0;
     g->last_vacuum_lod = o->vacuum_recovery ? 1 : 0;
-    const bool use_graph = !ctx->prof.enabled && st != nullptr && ctx->use_graphs;
+    const bool use_graph = !ctx->prof.enabled && st != nullptr && ctx->use_graphs && ctx->probe_cycles == 0;
     if (use_graph) {
         char key[256];
         snprintf(key, sizeof key, "%d/%d/%d/%d/%d/%d/%s", o->precision, o->scheme, o->richardson, o->n_steps,

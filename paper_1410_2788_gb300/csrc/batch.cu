@@ -89,8 +89,12 @@ static int plan_build(Ctx *ctx, Grid *const *grids, int n, const npb_opts *o, Ba
         const int dims[3] = {g0->geo.nx, g0->geo.ny, g0->geo.nz};
         bool ok = prec == NPB_FP32_SWEEP && o->eps_mode == NPB_EPS_HARMONIC && o->scheme <= NPB_LODIE2;
         for (int d = 0; d < 3; ++d) {
-            q.shape[d] = shape_for(ctx, prec, d, dims[d]);
-            ok = ok && q.shape[d].kind == 2 && tma_variant(d, q.shape[d].tx) >= 0;
+            bool tables = true;
+            for (Grid *g : q.grids)
+                for (int j = 0; j < nslot; ++j) tables = tables && g->h_legs[prec][slot_of(re, j)].line_tab[d];
+            q.shape[d] = usable_shape(shape_for(ctx, prec, d, dims[d]), d, dims[d], tables,
+                                      scheme_cn(o->scheme) ? FUSE_PRE_CN : 0);
+            ok = ok && (q.shape[d].kind == 2 || q.shape[d].kind == 3) && tma_variant(d, q.shape[d].tx) >= 0;
             for (Grid *g : q.grids) ok = ok && g->tma_ok[d];
         }
         q.table = ok;
@@ -162,8 +166,12 @@ static int group_step(Ctx *ctx, const BatchGroup &q, int n_legs, int prec, int s
         if (d == 0) flags = scheme == NPB_LODIE2 ? FUSE_PRE_SRC : FUSE_PRE_NL;
         if (d == 2 && scheme == NPB_LODIE2) flags = FUSE_POST_NL;
         if ((rc = pr.begin(st, &ev))) return rc;
-        CU(launch_sweep_inner_table(d, q.d_tab[d], n_legs, dims[0], dims[1], dims[2], g0->d_err, g0->tma_g[d], flags,
-                                    q.shape[d], ctx->sm_count, st));
+        if (q.shape[d].kind == 3)
+            CU(launch_sweep_line_table(d, q.d_tab[d], n_legs, dims[0], dims[1], dims[2], g0->d_err, g0->tma_g[d],
+                                       flags, q.shape[d], ctx->sm_count, st));
+        else
+            CU(launch_sweep_inner_table(d, q.d_tab[d], n_legs, dims[0], dims[1], dims[2], g0->d_err, g0->tma_g[d],
+                                        flags, q.shape[d], ctx->sm_count, st));
         if ((rc = pr.end(st, ev, K_SWEEP_X + d))) return rc;
     }
     if (scheme == NPB_LODIE1) {

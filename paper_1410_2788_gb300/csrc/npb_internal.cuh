@@ -53,7 +53,16 @@ struct LegDev {
     int32_t eps_mode;          // 0 harmonic, 1 midpoint
     float rEf[3], nl_qf, nl_omqf, srcf;  // the same constants rounded once to FP32 (FP32 sweeps)
     const int2 *ent_xq;                  // charge entries as (x | y << 16, FP32 qtilde), ent_x's order
+    // FP32 legs, per direction: the Thomas multipliers (m_j, cp_j) of a line whose half points all
+    // carry the leg's r*eps outside the molecule (r*eps_in for vacuum legs), j = 1 .. ceil((n-2)/2);
+    // the line-per-thread-pair sweeps use them on tiles of constant coefficients (null: no table)
+    const float2 *line_tab[3];
 };
+
+// Entries of one direction's multiplier table (n <= 288 nodes per line).
+constexpr int kLineTabMax = 144;
+// Lines per tile of the line-per-thread-pair sweeps.
+constexpr int kLineTX = 32;
 
 // One leg of an additive step (AOS/MAOS, Sec. 3.2-3.3): the states its combine stage reads.
 struct AddLeg {
@@ -81,7 +90,8 @@ enum : int {
 
 struct SweepShape {     // one instantiated line-solver shape
     int tx, seg, len;
-    int kind;           // 0: one tile per block, direct loads; 1: persistent TMA pipeline (FP32)
+    int kind;           // 0: one tile per block, direct loads; 1: persistent TMA pipeline (FP32);
+                        // 2: interior-row TMA segments (FP32); 3: a line per thread pair (FP32, y/z)
 };
 
 // Launchers (defined in sweep_*.cu).  Return cudaError of the launch.

@@ -79,6 +79,7 @@ struct npb_ctx {
     cudaStream_t own_stream = nullptr;
     cudaStream_t stream = nullptr;
     bool use_graphs = true;
+    long long probe_cycles = 0;     // > 0: failure-detection probe before every TMA sweep launch
     npb::Profiler prof;
     std::mutex tune_mu;
     std::map<int64_t, npb::SweepShape> tuned;  // autotuned line-solver shapes
@@ -138,6 +139,7 @@ struct npb_grid {
     void *d_u[2][4] = {};              // leg states by [precision][slot]
     int u_prec = -1;                   // precision of the last solve (for npb_potential)
     npb::LegDev *d_legs[2] = {};       // device leg tables by precision
+    float2 *d_line_tab = nullptr;      // FP32 legs: multiplier tables [slot][direction][kLineTabMax]
     npb::LegDev h_legs[2][4];
     std::string legs_key[2];
     // additive schemes (additive.cu): per slot the saved U^n, the x part and the y part; the
@@ -203,6 +205,7 @@ int grid_states(Grid *g, int prec, cudaStream_t st);
 int grid_prepare(Grid *g, const npb_opts *o, cudaStream_t st);
 LegDev make_leg(const Grid *g, int leg, const npb_opts *o);
 SweepShape shape_for(Ctx *ctx, int prec, int dir, int n);
+SweepShape usable_shape(SweepShape s, int dir, int n, bool tables, int flags);
 struct LegRef {
     Grid *g;
     int slot;

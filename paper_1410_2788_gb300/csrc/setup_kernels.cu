@@ -8,8 +8,8 @@
 //               order-dependent floating-point atomics: entries are bucketed by line,
 //               sorted by (x, atom, corner) and summed in that fixed order.
 //   boundary    Eq. (BoundaryCond) on the 6 faces: solvent uses eps_out and kbar,
-//               vacuum eps_in and kbar = 0.  FP64 pair terms, or FP32 pair terms with
-//               per-chunk FP64 accumulation for the mixed-precision path.
+//               vacuum eps_in and kbar = 0, both in one pass.  FP64 pair terms, or FP32 pair
+//               terms with per-chunk FP64 accumulation for the mixed-precision path.
 //
 // The distance tests and weights use explicitly rounded FP64 operations (no fused
 // multiply-add), so that inside/outside decisions and node charges are reproducible.
@@ -277,79 +277,6 @@ __device__ __forceinline__ void face_node(int64_t f, int nx, int ny, int nz, int
 
 constexpr int kAtomChunk = 256;
 
-// FP64 pair terms, summed in atom order: C sum_i q_i exp(-kbar d / sqrt(eps)) / (eps d).
-__global__ void k_boundary_f64(GridGeom g, const double *__restrict__ xyz, const double *__restrict__ q,
-                               int n_atoms, double eps, double kbar, double *__restrict__ out) {
-    __shared__ double sa[kAtomChunk][4];
-    const int64_t nf = face_count(g.nx, g.ny, g.nz);
-    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int i = 0, j = 0, k = 0;
-    if (f < nf) face_node(f, g.nx, g.ny, g.nz, i, j, k);
-    const double x = node_coord(g.ox, i, g.h), y = node_coord(g.oy, j, g.h), z = node_coord(g.oz, k, g.h);
-    const double ks = kbar / sqrt(eps);
-    double s = 0.0;
-    for (int a0 = 0; a0 < n_atoms; a0 += kAtomChunk) {
-        __syncthreads();
-        for (int t = threadIdx.x; t < kAtomChunk && a0 + t < n_atoms; t += blockDim.x) {
-            sa[t][0] = xyz[3 * (a0 + t)];
-            sa[t][1] = xyz[3 * (a0 + t) + 1];
-            sa[t][2] = xyz[3 * (a0 + t) + 2];
-            sa[t][3] = q[a0 + t];
-        }
-        __syncthreads();
-        const int na = min(kAtomChunk, n_atoms - a0);
-        if (ks == 0.0) {  // Coulomb faces: exp(0) = 1 exactly, so the sum is unchanged
-            for (int t = 0; t < na; ++t) {
-                const double dx = x - sa[t][0], dy = y - sa[t][1], dz = z - sa[t][2];
-                const double d = sqrt(dx * dx + dy * dy + dz * dz);
-                s += sa[t][3] / (eps * d);
-            }
-        } else {
-            for (int t = 0; t < na; ++t) {
-                const double dx = x - sa[t][0], dy = y - sa[t][1], dz = z - sa[t][2];
-                const double d = sqrt(dx * dx + dy * dy + dz * dz);
-                s += sa[t][3] * exp(-ks * d) / (eps * d);
-            }
-        }
-    }
-    if (f < nf) out[f] = kBjerrum * s;
-}
-
-// FP32 pair terms, each chunk summed in FP32 and chunks accumulated in FP64.
-__global__ void k_boundary_f32(GridGeom g, const double *__restrict__ xyz, const double *__restrict__ q,
-                               int n_atoms, double eps, double kbar, double *__restrict__ out) {
-    __shared__ float sa[kAtomChunk][4];
-    const int64_t nf = face_count(g.nx, g.ny, g.nz);
-    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int i = 0, j = 0, k = 0;
-    if (f < nf) face_node(f, g.nx, g.ny, g.nz, i, j, k);
-    // positions relative to the grid origin keep FP32 resolution near 1e-5 A
-    const float x = (float)(i * g.h), y = (float)(j * g.h), z = (float)(k * g.h);
-    const float ks = (float)(kbar / sqrt(eps));
-    const float ieps = (float)(1.0 / eps);
-    double s = 0.0;
-    for (int a0 = 0; a0 < n_atoms; a0 += kAtomChunk) {
-        __syncthreads();
-        for (int t = threadIdx.x; t < kAtomChunk && a0 + t < n_atoms; t += blockDim.x) {
-            sa[t][0] = (float)(xyz[3 * (a0 + t)] - g.ox);
-            sa[t][1] = (float)(xyz[3 * (a0 + t) + 1] - g.oy);
-            sa[t][2] = (float)(xyz[3 * (a0 + t) + 2] - g.oz);
-            sa[t][3] = (float)q[a0 + t];
-        }
-        __syncthreads();
-        const int na = min(kAtomChunk, n_atoms - a0);
-        float part = 0.f;
-        for (int t = 0; t < na; ++t) {
-            const float dx = x - sa[t][0], dy = y - sa[t][1], dz = z - sa[t][2];
-            const float d2 = dx * dx + dy * dy + dz * dz;
-            const float id = rsqrtf(d2);
-            part += sa[t][3] * __expf(-ks * d2 * id) * id;
-        }
-        s += (double)part;
-    }
-    if (f < nf) out[f] = kBjerrum * (double)ieps * s;
-}
-
 // Both media's faces in one pass, FP32 pair terms (chunk sums in FP32, chunks accumulated in
 // FP64): solvent C sum q exp(-kbar d / sqrt(eps_out)) / (eps_out d), vacuum C sum q / (eps_in d).
 // The two share the distance and its reciprocal square root; each thread holds kFaceBlock face
@@ -423,6 +350,58 @@ __global__ void k_boundary_pair_f32(GridGeom g, const double *__restrict__ xyz, 
         for (int r = 0; r < kFaceBlock; ++r) {
             ss[r] += (double)ps[r];
             sv[r] += (double)pv[r];
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < kFaceBlock; ++r) {
+        const int64_t f = f0 + (int64_t)r * blockDim.x;
+        if (f < nf) {
+            out_s[f] = kBjerrum / eps_s * ss[r];
+            out_v[f] = kBjerrum / eps_v * sv[r];
+        }
+    }
+}
+
+// Both media's faces in one pass, FP64 pair terms (the parity path): the two sums share the
+// distance, taken as d^2 * rsqrt(d^2), and 1/d = rsqrt(d^2); only the solvent's screening needs its
+// exponential.  Each thread holds kFaceBlock face nodes; the atoms are summed in index order.
+__global__ void k_boundary_pair_f64(GridGeom g, const double *__restrict__ xyz, const double *__restrict__ q,
+                                    int n_atoms, double eps_s, double kbar, double eps_v,
+                                    double *__restrict__ out_s, double *__restrict__ out_v) {
+    __shared__ double4 sa[kAtomChunk];
+    const int64_t nf = face_count(g.nx, g.ny, g.nz);
+    const int64_t f0 = (int64_t)blockIdx.x * blockDim.x * kFaceBlock + threadIdx.x;
+    double x[kFaceBlock], y[kFaceBlock], z[kFaceBlock];
+#pragma unroll
+    for (int r = 0; r < kFaceBlock; ++r) {
+        int i = 0, j = 0, k = 0;
+        const int64_t f = f0 + (int64_t)r * blockDim.x;
+        if (f < nf) face_node(f, g.nx, g.ny, g.nz, i, j, k);
+        x[r] = node_coord(g.ox, i, g.h);
+        y[r] = node_coord(g.oy, j, g.h);
+        z[r] = node_coord(g.oz, k, g.h);
+    }
+    const double ks = kbar / sqrt(eps_s);
+    double ss[kFaceBlock], sv[kFaceBlock];
+#pragma unroll
+    for (int r = 0; r < kFaceBlock; ++r) ss[r] = sv[r] = 0.0;
+    for (int a0 = 0; a0 < n_atoms; a0 += kAtomChunk) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < kAtomChunk && a0 + t < n_atoms; t += blockDim.x)
+            sa[t] = make_double4(xyz[3 * (a0 + t)], xyz[3 * (a0 + t) + 1], xyz[3 * (a0 + t) + 2], q[a0 + t]);
+        __syncthreads();
+        const int na = min(kAtomChunk, n_atoms - a0);
+        for (int t = 0; t < na; ++t) {
+            const double4 A = sa[t];
+#pragma unroll
+            for (int r = 0; r < kFaceBlock; ++r) {
+                const double dx = x[r] - A.x, dy = y[r] - A.y, dz = z[r] - A.z;
+                const double d2 = dx * dx + dy * dy + dz * dz;
+                const double id = rsqrt(d2);
+                const double qi = A.w * id;
+                sv[r] += qi;
+                ss[r] += ks == 0.0 ? qi : qi * exp(-ks * (d2 * id));
+            }
         }
     }
 #pragma unroll
@@ -540,8 +519,10 @@ cudaError_t setup_charges(const GridGeom &g, const double *xyz, const double *q,
                           double *ent_qt, int64_t *ent_off, int2 *ent_xq, cudaStream_t st) {
     const int n_lines = g.ny * g.nz;
     const int n_raw = 8 * n_atoms;
-    cudaMemsetAsync(s.count, 0, sizeof(int32_t) * n_lines, st);
-    cudaMemsetAsync(s.fill, 0, sizeof(int32_t) * n_lines, st);
+    // the per-line counters are accumulated into: a refused clear must not leave stale counts
+    cudaError_t e = cudaMemsetAsync(s.count, 0, sizeof(int32_t) * n_lines, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.fill, 0, sizeof(int32_t) * n_lines, st);
+    if (e != cudaSuccess) return e;
     if (n_raw > 0) k_charge_raw<<<blocks_for(n_raw, 256), 256, 0, st>>>(g, xyz, q, n_atoms, s.raw, s.count);
     k_scan_lines<<<1, 1024, 0, st>>>(s.count, s.raw_begin, n_lines, nullptr);
     if (n_raw > 0)
@@ -554,21 +535,17 @@ cudaError_t setup_charges(const GridGeom &g, const double *xyz, const double *q,
     return cudaGetLastError();
 }
 
-cudaError_t setup_boundary(const GridGeom &g, const double *xyz, const double *q, int n_atoms, double eps,
-                           double kbar, bool fp32_pairs, double *out, cudaStream_t st) {
-    const int64_t nf = face_count(g.nx, g.ny, g.nz);
-    const int t = 128;
-    if (fp32_pairs) k_boundary_f32<<<blocks_for(nf, t), t, 0, st>>>(g, xyz, q, n_atoms, eps, kbar, out);
-    else k_boundary_f64<<<blocks_for(nf, t), t, 0, st>>>(g, xyz, q, n_atoms, eps, kbar, out);
-    return cudaGetLastError();
-}
-
 cudaError_t setup_boundary_pair(const GridGeom &g, const double *xyz, const double *q, int n_atoms, double eps_out,
-                                double kbar, double eps_in, double *out_s, double *out_v, cudaStream_t st) {
+                                double kbar, double eps_in, double *out_s, double *out_v, cudaStream_t st,
+                                bool fp64) {
     const int64_t nf = face_count(g.nx, g.ny, g.nz);
     const int t = 128;
-    k_boundary_pair_f32<<<blocks_for(nf, (int64_t)t * kFaceBlock), t, 0, st>>>(g, xyz, q, n_atoms, eps_out, kbar,
-                                                                               eps_in, out_s, out_v);
+    if (fp64)
+        k_boundary_pair_f64<<<blocks_for(nf, (int64_t)t * kFaceBlock), t, 0, st>>>(g, xyz, q, n_atoms, eps_out, kbar,
+                                                                                   eps_in, out_s, out_v);
+    else
+        k_boundary_pair_f32<<<blocks_for(nf, (int64_t)t * kFaceBlock), t, 0, st>>>(g, xyz, q, n_atoms, eps_out, kbar,
+                                                                                   eps_in, out_s, out_v);
     return cudaGetLastError();
 }
 

@@ -33,12 +33,11 @@ cudaError_t setup_mask(const GridGeom &g, const double *xyz, const double *radiu
 cudaError_t setup_charges(const GridGeom &g, const double *xyz, const double *q, int n_atoms,
                           ChargeScratch &s, int32_t *line_begin, int32_t *line_count, int32_t *ent_x,
                           double *ent_qt, int64_t *ent_off, int2 *ent_xq, cudaStream_t st);
-cudaError_t setup_boundary(const GridGeom &g, const double *xyz, const double *q, int n_atoms, double eps,
-                           double kbar, bool fp32_pairs, double *out, cudaStream_t st);
 // Both media's faces in one pass with FP32 pair terms: solvent (eps_out, kbar) into out_s,
 // vacuum (eps_in, Coulomb) into out_v.
 cudaError_t setup_boundary_pair(const GridGeom &g, const double *xyz, const double *q, int n_atoms, double eps_out,
-                                double kbar, double eps_in, double *out_s, double *out_v, cudaStream_t st);
+                                double kbar, double eps_in, double *out_s, double *out_v, cudaStream_t st,
+                                bool fp64 = false);
 cudaError_t init_leg(int prec, const GridGeom &g, const double *bc, void *u, cudaStream_t st);
 cudaError_t unpad_state(int prec, const GridGeom &g, const void *u, double *out, cudaStream_t st);
 cudaError_t pad_state(int prec, const GridGeom &g, const double *in, void *u, cudaStream_t st);

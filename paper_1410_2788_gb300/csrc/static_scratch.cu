@@ -1,18 +1,18 @@
 // static_scratch.cu -- npb_charge_list_static: the charge-list build without any allocation.
 //
-// Some callers cannot allocate device memory at the moment they need a charge list:
-// code in the middle of capturing a CUDA graph (cudaMalloc is not allowed there), host
-// applications that own all device memory through their own pool and do not let
-// libraries call cudaMalloc, and latency-critical paths that cannot afford cudaMalloc's
-// implicit synchronisation.  This entry point builds the same x-line-grouped trilinear
-// charge list as npb_grid_create, into device buffers the caller provides, and takes every
-// temporary it needs from one fixed array in this file's device memory.
+// Some callers cannot allocate device memory at the moment they need a charge list: host
+// applications that own all device memory through their own pool and do not let libraries
+// call cudaMalloc, and latency-critical paths that cannot afford the implicit device
+// synchronisation of cudaMalloc/cudaFree.  This entry point builds the same x-line-grouped
+// trilinear charge list as npb_grid_create, into device buffers the caller provides, and
+// takes every temporary it needs from one fixed array in this file's device memory.
 //
-// The array lives as long as the library is loaded, on every GPU that loads it.  The
-// first call on a device looks up its address with cudaGetSymbolAddress (which may load
-// the module); make that first call before any stream capture.  All calls share the
-// array, so calls whose work overlaps on the GPU (different streams, or different host
-// threads, on one device) race and must be serialised by the caller.
+// The array lives as long as the library is loaded, on every GPU that loads it.  The first
+// call on a device looks up the array's device address with cudaGetSymbolAddress, with that
+// device current; host code never hands the array's name itself to a kernel.  All calls
+// share the array and each call clears the counters it accumulates into, so calls whose work
+// overlaps on the GPU (different streams, or different host threads, on one device) race and
+// must be serialised by the caller.
 #include <cmath>
 #include <mutex>
 

@@ -75,6 +75,52 @@ __device__ __forceinline__ float nl_flow(float w, float q, float omq) {
     return copysignf(__logf(num * fast_rcp(den)), w);
 }
 
+// The nonlinear flow of Eq. (ana3) for small q = exp(-kbar^2 tau): with e = exp(-|w|),
+// t = tanh(|w|/2) = (1 - e)/(1 + e), x = q t <= q, and |w'| = 2 atanh(x) = 2x (1 + x^2/3 + x^4/5
+// + x^6/7 + ...), truncated after x^6/7 (relative error below x^8/9 <= 2e-11 for q <= 1/16): two
+// special-function operations instead of three.
+__device__ __forceinline__ float nl_flow_series(float w, float q) {
+    const float e = __expf(-fabsf(w));
+    const float t = (1.0f - e) * fast_rcp(1.0f + e);
+    const float x = q * t, x2 = x * x;
+    const float s = fmaf(x2, fmaf(x2, fmaf(x2, 1.0f / 7.0f, 0.2f), 1.0f / 3.0f), 1.0f);
+    return copysignf(2.0f * x * s, w);
+}
+
+// q at or below which the series form is used (a leg-uniform choice).
+constexpr float kNlSeriesMaxQ = 0.0625f;
+
+// FP64 flavour of the series: t = -expm1(-|w|) / (2 + expm1(-|w|)) and 2 atanh(x) to x^15/15
+// (relative truncation error below x^16/17 < 4e-21 for q <= 1/16), in place of log1p and one of the
+// two divisions of nl_flow.
+__device__ __forceinline__ double nl_flow_series(double w, double q) {
+    const double em = expm1(-fabs(w));
+    const double x = q * (-em / (2.0 + em)), x2 = x * x;
+    double s = 1.0 / 15.0;
+    s = fma(s, x2, 1.0 / 13.0);
+    s = fma(s, x2, 1.0 / 11.0);
+    s = fma(s, x2, 1.0 / 9.0);
+    s = fma(s, x2, 1.0 / 7.0);
+    s = fma(s, x2, 1.0 / 5.0);
+    s = fma(s, x2, 1.0 / 3.0);
+    s = fma(s, x2, 1.0);
+    return copysign(2.0 * x * s, w);
+}
+
+// The nonlinear stage with the leg's q.  FP64: the series where q is small (it replaces log1p and a
+// division), else the closed form.  FP32: the three-operation closed form (the two-operation series
+// plus its polynomial measured slower on the interior-row sweeps).
+template <typename T>
+__device__ __forceinline__ T nl_flow_leg(T w, T q, T omq);
+template <>
+__device__ __forceinline__ double nl_flow_leg<double>(double w, double q, double omq) {
+    return q <= (double)kNlSeriesMaxQ ? nl_flow_series(w, q) : nl_flow(w, q, omq);
+}
+template <>
+__device__ __forceinline__ float nl_flow_leg<float>(float w, float q, float omq) {
+    return nl_flow(w, q, omq);
+}
+
 template <typename T>
 struct Vec16;
 template <>
@@ -373,7 +419,7 @@ __global__ void __launch_bounds__(TX *SEG)
             if (DIR == DIR_X) v = tile[line * S + g];
             else v = u[base + g * stride];
             if ((flags & FUSE_PRE_NL) && nl_on && g >= 1 && g <= ndir - 2 && ((nb >> (k + 1)) & 1u) == 0u)
-                v = nl_flow(v, nlq, nlomq);
+                v = nl_flow_leg(v, nlq, nlomq);
         }
         al[k] = v;
     }
@@ -445,7 +491,7 @@ __global__ void __launch_bounds__(TX *SEG)
 #pragma unroll
             for (int k = 0; k < L; ++k) {
                 T x = k == 0 ? F : (k == L - 1 ? E : al[k] + be[k] * F + ga[k] * E);
-                if (nl_all) x = nl_flow(x, nlq, nlomq);
+                if (nl_all) x = nl_flow_leg(x, nlq, nlomq);
                 u[base + (g0 + k) * stride] = x;
             }
         } else {
@@ -454,7 +500,7 @@ __global__ void __launch_bounds__(TX *SEG)
                 const int g = g0 + k;
                 if (g >= 1 && g <= ndir - 2) {
                     T x = k == 0 ? F : (k == L - 1 ? E : al[k] + be[k] * F + ga[k] * E);
-                    if (post_nl && ((nb >> (k + 1)) & 1u) == 0u) x = nl_flow(x, nlq, nlomq);
+                    if (post_nl && ((nb >> (k + 1)) & 1u) == 0u) x = nl_flow_leg(x, nlq, nlomq);
                     u[base + g * stride] = x;
                 }
             }

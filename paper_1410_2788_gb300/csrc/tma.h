@@ -7,6 +7,7 @@
 namespace npb {
 
 struct TmaLaunch;
+struct LegTma;
 
 struct TmaGeom {
     bool ok;
@@ -38,5 +39,21 @@ cudaError_t launch_sweep_inner(int dir, TmaLaunch &P, const TmaGeom &g, int flag
                             cudaStream_t st);
 cudaError_t prepare_sweep_inner();
 int inner_shapes(int dir, SweepShape *out, int max);
+// The cheapest interior-row shape covering the n-2 unknowns of a line along dir.
+SweepShape inner_default_shape(int dir, int n);
+
+// Line-per-thread-pair sweeps (kind 3): y/z tiles of 32 lines; `len` of the shape is the number of
+// pipeline stages (1 or 2).  Every leg needs its multiplier table (LegDev::line_tab).
+cudaError_t launch_sweep_line(int dir, TmaLaunch &P, const TmaGeom &g, int flags, SweepShape s, int sm_count,
+                              cudaStream_t st);
+cudaError_t launch_sweep_line_table(int dir, const LegTma *table, int n_legs, int nx, int ny, int nz,
+                                    int32_t *err, const TmaGeom &g, int flags, SweepShape s, int sm_count,
+                                    cudaStream_t st);
+cudaError_t prepare_sweep_line();
+// Failure-detection probe: waits, with the sweeps' bounded-wait helper and a bound of `limit` SM
+// cycles, on a barrier that nothing arrives at, and sets *err as an expired sweep wait does.
+cudaError_t launch_wait_probe(int32_t *err, long long limit, int sm_count, cudaStream_t st);
+int line_shapes(int dir, SweepShape *out, int max);
+void line_table(double e, int n, float2 *out);
 
 }  // namespace npb

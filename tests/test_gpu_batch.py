@@ -91,3 +91,42 @@ def test_batch_after_destroy_and_invalid(npb):
             npb.npb_grid_destroy(g)
     finally:
         npb.npb_ctx_destroy(c)
+
+
+def test_batch_with_tuned_shapes_and_tuning_cache(npb, O, tmp_path):
+    """The autotuner picks the line solver per (direction, grid size) -- the candidates span the
+    paper's Thomas per line (kind 3) and the segmented Thomas/PCR hybrids -- the picks survive a save/load round trip through the tuning cache, and the batched energies
+    with those shapes still equal the single solves bit for bit and the oracle to 1e-4."""
+    mols = _mols()
+    c = npb.npb_ctx_create(0, 0)
+    try:
+        grids = [npb.npb_grid_create(c, p) for p in mols]
+        try:
+            o = npb.make_opts(0.4, 0.04, 6, precision=1)
+            seen = set()
+            for p, g in zip(mols, grids):
+                if p.n[0] not in seen:
+                    seen.add(p.n[0])
+                    rep = npb.npb_autotune(g, o, reps=2)
+                    kinds = {r["kind"] for r in rep}
+                    assert {2, 3} <= kinds, kinds  # hybrids and the line-per-thread-pair Thomas
+            shapes = {(d, n): npb.npb_tune_get(c, 1, d, n) for n in seen for d in range(3)}
+            path = str(tmp_path / "tune.json")
+            npb.npb_tune_save(c, path)
+            single = [npb.npb_energy(g, o) for g in grids]
+            batch = npb.npb_energy_batch(grids, o)
+            assert batch == single
+        finally:
+            for g in grids:
+                npb.npb_grid_destroy(g)
+    finally:
+        npb.npb_ctx_destroy(c)
+    c2 = npb.npb_ctx_create(0, 0)
+    try:
+        assert npb.npb_tune_load(c2, path) == len(shapes)
+        assert {k: npb.npb_tune_get(c2, 1, k[0], k[1]) for k in shapes} == shapes
+    finally:
+        npb.npb_ctx_destroy(c2)
+    for p, v in zip(mols[:2], batch[:2]):
+        ref = O.energy(p, 10.0, 6)
+        assert abs(v - ref) <= 1e-4 * abs(ref), (v, ref)

@@ -1,7 +1,8 @@
 """The charge-list entry point that allocates nothing, against the allocating one.
 
-Some callers cannot allocate device memory when they need a charge list (for example
-while capturing a CUDA graph, or inside an application whose own pool owns the device).
+Some callers cannot allocate device memory when they need a charge list (an application
+whose own pool owns the device, or a latency-critical path that cannot take the implicit
+synchronisation of cudaMalloc/cudaFree).
 npb_charge_list_static serves them from a fixed array inside the library.  This file is
 collected last on purpose, so that a run stopping at its first failure has already run
 every other test; it also passes on its own in a fresh process.
