@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(TX *SEG, inner_min_blocks<TX * SEG>())
         if (!pre_cn && nrem >= 1 && nrem <= L) {  // (Crank-Nicolson: in registers after the explicit half)
             const int k = nrem - 1;
             T v = D[at(g0 + k)];
-            if (pre_nl && ((flow >> k) & 1u)) v = nl_flow(v, nlq, nlomq);
+            if (pre_nl && ((flow >> k) & 1u)) v = nl_flow_leg(v, nlq, nlomq);
             const T etop = ((both >> nrem) & 1u) ? rE2 : (((any >> nrem) & 1u) ? rE1 : rE0);
             D[at(g0 + k)] = v + etop * D[at(g0 + k + 1)];
             flow &= ~(1u << k);
@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(TX *SEG, inner_min_blocks<TX * SEG>())
             if (pre_nl) {  // uniform over the tile: the flow code is not issued for other sweeps
 #pragma unroll
                 for (int k = 0; k < L; ++k)
-                    if ((flow >> k) & 1u) al[k] = nl_flow(al[k], nlq, nlomq);
+                    if ((flow >> k) & 1u) al[k] = nl_flow_leg(al[k], nlq, nlomq);
             }
             if constexpr (pre_cn) {
                 // the explicit half w_k + e_{k+1/2} (w_{k+1} - w_k) - e_{k-1/2} (w_k - w_{k-1}) from the
@@ -330,8 +330,8 @@ __global__ void __launch_bounds__(TX *SEG, inner_min_blocks<TX * SEG>())
                 T wprev = nrem > 0 ? D[at(g0 - 1)] : T(0);
                 T wtop = nrem >= L ? D[at(g0 + L)] : T(0);
                 if (pre_nl) {  // LODCN1: the neighbours take the inflowing nonlinear stage too
-                    if (seg > 0 && nrem > 0 && !(nb & 1u)) wprev = nl_flow(wprev, nlq, nlomq);
-                    if (nrem > L && !((nb >> (L + 1)) & 1u)) wtop = nl_flow(wtop, nlq, nlomq);
+                    if (seg > 0 && nrem > 0 && !(nb & 1u)) wprev = nl_flow_leg(wprev, nlq, nlomq);
+                    if (nrem > L && !((nb >> (L + 1)) & 1u)) wtop = nl_flow_leg(wtop, nlq, nlomq);
                 }
                 if (!FULL) {
 #pragma unroll
@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(TX *SEG, inner_min_blocks<TX * SEG>())
             const uint32_t post = ~(nb >> 1) & (nrem >= 32 ? 0xffffffffu : (nrem > 0 ? (1u << nrem) - 1u : 0u));
 #pragma unroll
             for (int k = 0; k < L; ++k)
-                if ((post >> k) & 1u) al[k] = nl_flow(al[k], nlq, nlomq);
+                if ((post >> k) & 1u) al[k] = nl_flow_leg(al[k], nlq, nlomq);
         }
         if (warp_full) {
 #pragma unroll

@@ -107,9 +107,25 @@ __device__ __forceinline__ double nl_flow_series(double w, double q) {
     return copysign(2.0 * x * s, w);
 }
 
+__device__ __forceinline__ float tanh_approx(float x) {
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// FP32 flow for small q from the hardware tanh: x = 2 q tanh(w/2) (|x| <= 2q <= 1/8) and
+// w' = 2 atanh(x/2) = x (1 + x^2/12 + x^4/80 + ...), truncated after x^4/80 (relative error below
+// x^6/448 < 1e-8).  tanh.approx.f32 carries a relative error near 2^-11, so |w'| is off by at most
+// 5e-4 of itself: at most 1e-6 kT/e on a leg with tau = 10 (q = 2.2e-4) and 1.5e-5 kT/e with tau = 5
+// (q = 0.015), far inside the FP32 path's tolerance.  One special-function operation and five others.
+__device__ __forceinline__ float nl_flow_tanh(float w, float q2) {
+    const float x = q2 * tanh_approx(0.5f * w);
+    const float x2 = x * x;
+    return x * fmaf(x2, fmaf(x2, 1.0f / 80.0f, 1.0f / 12.0f), 1.0f);
+}
+
 // The nonlinear stage with the leg's q.  FP64: the series where q is small (it replaces log1p and a
-// division), else the closed form.  FP32: the three-operation closed form (the two-operation series
-// plus its polynomial measured slower on the interior-row sweeps).
+// division), else the closed form.  FP32: the tanh form where q is small, else the closed form.
 template <typename T>
 __device__ __forceinline__ T nl_flow_leg(T w, T q, T omq);
 template <>
@@ -118,7 +134,7 @@ __device__ __forceinline__ double nl_flow_leg<double>(double w, double q, double
 }
 template <>
 __device__ __forceinline__ float nl_flow_leg<float>(float w, float q, float omq) {
-    return nl_flow(w, q, omq);
+    return q <= kNlSeriesMaxQ ? nl_flow_tanh(w, 2.0f * q) : nl_flow(w, q, omq);
 }
 
 template <typename T>
