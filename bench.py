@@ -446,6 +446,24 @@ def roofline_traffic(kernel: str, workload: str):
     return e.get("dram_bytes_per_launch")
 
 
+def fp64_roofline(point_steps_per_s, dfma_per_s, ddiv_per_s):
+    """The plain FP64 path against the FP64 units: FP64 flops per interior point-step counted by ncu
+    on the FP64 sweeps (profiles/ncu_fp64_ops.json, when it matches the kernel source) times the
+    measured point-steps/s, over twice the measured FMA rate (npb_measure_fp64).  The whole step is
+    timed, set-up included, so the fraction understates the sweeps' own."""
+    out = {"bound": "alu", "unit": "GFLOP/s", "peak": 2 * dfma_per_s / 1e9, "peak_source": "measured",
+           "measured_dfma_per_s": dfma_per_s, "measured_ddiv_per_s": ddiv_per_s}
+    path = os.path.join(ROOT, "profiles", "ncu_fp64_ops.json")
+    e = json.load(open(path)).get("protein_1k") if os.path.exists(path) else None
+    if e and e.get("source_hash") == _kernel_source_hash():
+        flops = sum(e["flops_per_node_sweep"].values())
+        out.update(achieved=flops * point_steps_per_s / 1e9, frac=flops * point_steps_per_s / (2 * dfma_per_s),
+                   flops_per_point_step=flops, fp64_pipe_busy_ncu=e["fp64_pipe_busy"])
+    else:
+        out.update(achieved=None, frac=None)
+    return out
+
+
 def sweep_roofline(npb, grid, opts, problem, w, elem, peak, peak_kind, workload_name):
     """The dominant sweep kernel against the HBM roofline, timed the way the solve runs it: each
     direction's 4-leg and 2-leg launches as graph-captured back-to-back launches (CUDA events on
@@ -585,10 +603,11 @@ def run_ours(args):
     want_errors = world == 1 and rank == 0 and args.cpu_baseline
     legs32 = fp32_errors(npb, grid, problem, npb.grid_shape(problem)) if want_errors else None
 
-    # ---- the plain FP64 path on the same molecule
+    # ---- the plain FP64 path on the same molecule, and the FP64 units' measured rates
     k64 = max(2, min(3, args.steps))
     ms64, dg64 = timed(opts64, k64)
     t64, u64 = aggregate(sum(ms64) / 1e3, units_per_step * k64, world)
+    dfma_s, ddiv_s = npb.npb_measure_fp64(ctx)
 
     # ---- launches per step and per-kernel shares (events around every launch, no graph)
     npb.npb_ctx_profile(ctx, True)
@@ -676,8 +695,9 @@ def run_ours(args):
                        parallelism=f"replicas x{world}"),
         "dG_kcal_mol": dg,
         "solves_per_s": args.steps * world / total_s,
-        "fp64_path": {"value": u64 / t64 / 1e6, "unit": UNIT, "ms_per_step": 1e3 * t64 / k64,
-                      "solves_per_s": k64 * world / t64, "dG_kcal_mol": dg64},
+        "fp64_path": dict({"value": u64 / t64 / 1e6, "unit": UNIT, "ms_per_step": 1e3 * t64 / k64,
+                           "solves_per_s": k64 * world / t64, "dG_kcal_mol": dg64},
+                          roofline=fp64_roofline(u64 / t64, dfma_s, ddiv_s)),
         "error_vs_oracle": errors,
         "wall_s_timed_region": wall,
         "roofline": roofline,

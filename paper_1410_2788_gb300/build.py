@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "libnpb.so")
 
 SOURCES = ["api.cu", "serve.cu", "setup_kernels.cu", "stage_kernels.cu", "sweep_f32.cu", "sweep_f64.cu",
            "tune.cu", "static_scratch.cu", "sweep_tma_f32.cu", "sweep_inner_x.cu", "sweep_inner_y.cu", "sweep_inner_z.cu",
-           "batch.cu", "fft_vacuum.cu", "additive.cu", "sweep_line_f32.cu", "measure.cu"]
+           "batch.cu", "fft_vacuum.cu", "additive.cu", "sweep_line_f32.cu", "measure.cu", "sweep_line64.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
                 "-diag-suppress", "20040"]

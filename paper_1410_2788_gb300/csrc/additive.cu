@@ -82,7 +82,10 @@ int additive_prepare(Grid *g, const npb_opts *o, cudaStream_t st) {
             D.src = share[d] * L.src;
             D.srcf = (float)D.src;
             D.nl_on = 0;
-            for (int i = 0; i < 3; ++i) D.line_tab[i] = nullptr;  // tables of the unscaled r*eps
+            for (int i = 0; i < 3; ++i) {  // tables and multipliers of the unscaled r*eps
+                D.line_tab[i] = nullptr;
+                D.fac[i] = nullptr;
+            }
             g->h_sub[prec][d][s] = D;
         }
         const bool half = leg == NPB_LEG_SOLVENT_HALF || leg == NPB_LEG_VACUUM_HALF;
@@ -117,7 +120,7 @@ int additive_prepare(Grid *g, const npb_opts *o, cudaStream_t st) {
 static cudaError_t directional_sweep(Grid *g, int prec, int d, int slot0, int n, cudaStream_t st) {
     const int n3[3] = {g->geo.nx, g->geo.ny, g->geo.nz};
     // the directional legs carry scaled r*eps and no multiplier tables
-    SweepShape shape = usable_shape(shape_for(g->ctx, prec, d, n3[d]), d, n3[d], false, 0);
+    SweepShape shape = usable_shape(shape_for(g->ctx, prec, d, n3[d]), d, n3[d], false, 0, prec);
     const int v = tma_variant(d, shape.tx);
     if (shape.kind >= 1 && prec == NPB_FP32_SWEEP && g->tma_ok[d] && v >= 0 && n <= kTmaMaxLegs &&
         g->h_sub[prec][d][slot0].eps_mode == 0) {

@@ -343,6 +343,7 @@ extern "C" size_t npb_grid_footprint(const npb_problem *p, int32_t precision) {
     const size_t raw = std::max<size_t>(1, 8 * na);
     size_t b = 0;
     b += 4 * state_bytes(p->n, precision);                                   // four leg states
+    if (precision == NPB_FP64) b += 12 * state_bytes(p->n, precision);       // their multipliers
     b += (size_t)mask_words_per_row((int)pitch) * lines * 4;                 // node mask
     b += nz * nx * line_words((int)ny) * 4 + ny * nx * line_words((int)nz) * 4;  // line-major masks
     b += 2 * lines * 4 + raw * (4 + 8 + 8 + 8);                              // charge list
@@ -466,6 +467,7 @@ int npb::grid_setup(npb_grid *g, cudaStream_t st) {
     for (int m = 0; m < 2; ++m)
         for (int k = 0; k < 2; ++k) g->bc_valid[m][k] = false;
     g->vac_fft_valid = false;
+    g->fac_valid = false;  // the mask may have changed
     return 0;
 }
 
@@ -536,6 +538,10 @@ int npb::grid_states(npb_grid *g, int prec, cudaStream_t st) {
     int rc = galloc(g, &g->d_legs[prec], 4);
     if (rc) return rc;
     if (prec == NPB_FP32_SWEEP && (rc = galloc(g, &g->d_line_tab, (size_t)4 * 3 * kLineTabMax))) return rc;
+    if (prec == NPB_FP64)
+        for (int s = 0; s < 4; ++s)
+            for (int d = 0; d < 3; ++d)
+                if ((rc = galloc(g, &g->d_fac[s][d], bytes / sizeof(double)))) return rc;
     g->legs_key[prec] = "";
     return 0;
 }
@@ -561,9 +567,13 @@ LegDev npb::make_leg(const npb_grid *g, int leg, const npb_opts *o) {
     L.ent_xq = g->d_ent_xq;
     L.src = tau * 4.0 * kPi * kBjerrum / (h * h * h);
     L.eps_mode = o->eps_mode == NPB_EPS_MIDPOINT ? 1 : 0;
+    for (int d = 0; d < 3; ++d) L.fac[d] = prec == NPB_FP64 ? g->d_fac[kLegSlot[leg]][d] : nullptr;
     if (solvent) {
         const double ei = g->eps_in, eo = g->eps_out;
         L.mask = g->d_mask;
+        L.lmask[0] = g->d_mask;
+        L.lmask[1] = g->d_mask_y;
+        L.lmask[2] = g->d_mask_z;
         L.rE[0] = r * eo;
         L.rE[1] = r * (2.0 * ei * eo / (ei + eo));
         L.rE[2] = r * ei;
@@ -573,6 +583,7 @@ LegDev npb::make_leg(const npb_grid *g, int leg, const npb_opts *o) {
         L.nl_omq = -std::expm1(-g->kappa2 * tau);
     } else {
         L.mask = nullptr;
+        for (int d = 0; d < 3; ++d) L.lmask[d] = nullptr;
         L.rE[0] = L.rE[1] = L.rE[2] = r * g->eps_in;
         for (int d = 0; d < 3; ++d) L.half[d] = nullptr;
         L.nl_on = 0;
@@ -630,6 +641,13 @@ int npb::grid_prepare(npb_grid *g, const npb_opts *o, cudaStream_t st) {
         CU(cudaMemcpyAsync(g->d_legs[prec], g->h_legs[prec], sizeof(LegDev) * 4, cudaMemcpyHostToDevice, st));
         CU(cudaStreamSynchronize(st));
         g->legs_key[prec] = key;
+        if (prec == NPB_FP64) g->fac_valid = false;
+    }
+    if (prec == NPB_FP64 && !g->fac_valid && o->eps_mode == NPB_EPS_HARMONIC) {
+        // the FP64 line solver's multipliers: once per legs and mask, before any graph capture
+        for (int d = 0; d < 3; ++d)
+            CU(launch_line64_factors(d, g->d_legs[prec], 4, g->geo.nx, g->geo.ny, g->geo.nz, st));
+        g->fac_valid = true;
     }
     return scheme_additive(o->scheme) ? additive_prepare(g, o, st) : 0;
 }
@@ -646,14 +664,18 @@ SweepShape npb::shape_for(npb_ctx *ctx, int prec, int dir, int n) {
         const SweepShape best = inner_default_shape(dir, n);
         if (best.tx) return best;
     }
+    // FP64: Thomas per line with the multipliers computed once per leg (FP64-unit bound: the fewest
+    // FP64 operations per node)
+    if (prec == NPB_FP64) return SweepShape{32, 2, 1, 3};
     return default_sweep_shape(prec, dir, n);
 }
 
 // The shape a launch can take for legs that cannot use `s`: the line-per-thread-pair kernel needs
 // every leg's multiplier table and runs the implicit-Euler sweeps only (no fused Crank-Nicolson
 // half step); those legs take the interior-row segments instead.
-SweepShape npb::usable_shape(SweepShape s, int dir, int n, bool tables, int flags) {
-    if (s.kind == 3 && (!tables || (flags & FUSE_PRE_CN))) return inner_default_shape(dir, n);
+SweepShape npb::usable_shape(SweepShape s, int dir, int n, bool tables, int flags, int prec) {
+    if (s.kind == 3 && prec == NPB_FP64 && !tables) return default_sweep_shape(prec, dir, n);
+    if (s.kind == 3 && prec != NPB_FP64 && (!tables || (flags & FUSE_PRE_CN))) return inner_default_shape(dir, n);
     return s;
 }
 
@@ -708,6 +730,9 @@ cudaError_t npb::launch_dir(npb_grid *g, int prec, int d, SweepShape shape, int 
         if (shape.kind == 2) return launch_sweep_inner(d, P, g->tma_g[d], flags, shape, g->ctx->sm_count, st);
         return launch_sweep_tma(d, P, g->tma_g[d], flags, shape, g->ctx->sm_count, st);
     }
+    if (shape.kind == 3 && prec == NPB_FP64 && g->fac_valid && g->h_legs[prec][slot0].eps_mode == 0 &&
+        !(flags & FUSE_PRE_CN))
+        return launch_sweep_line64(d, g->d_legs[prec] + slot0, n_legs, nx, ny, nz, flags, st);
     if (shape.kind >= 1) shape = default_sweep_shape(prec, d, n_dir[d]);
     return launch_sweep(prec, d, g->d_legs[prec] + slot0, n_legs, nx, ny, nz, flags, shape, st);
 }
@@ -732,12 +757,18 @@ int npb::step_legs(npb_ctx *ctx, const LegRef *refs, int n, const LegDev *d_tabl
         shape[d] = shape_for(ctx, prec, d, n_dir[d]);
         bool tables = true;
         for (int i = 0; i < n; ++i) tables = tables && refs[i].g->h_legs[prec][refs[i].slot].line_tab[d] != nullptr;
-        shape[d] = usable_shape(shape[d], d, n_dir[d], tables, cn_scheme ? FUSE_PRE_CN : 0);
+        if (prec == NPB_FP64) {  // the multipliers exist for harmonic-eps legs of prepared grids
+            tables = true;
+            for (int i = 0; i < n; ++i)
+                tables = tables && refs[i].g->fac_valid && refs[i].g->h_legs[prec][refs[i].slot].eps_mode == 0;
+        }
+        shape[d] = usable_shape(shape[d], d, n_dir[d], tables, cn_scheme ? FUSE_PRE_CN : 0, prec);
         bool ok = shape[d].kind >= 1 && prec == NPB_FP32_SWEEP;
         for (int i = 0; i < n && ok; ++i)
             ok = refs[i].g->tma_ok[d] && refs[i].g->h_legs[prec][refs[i].slot].eps_mode == 0;
         tma[d] = ok && tma_variant(d, shape[d].tx) >= 0;
-        if (shape[d].kind >= 1 && !tma[d]) shape[d] = default_sweep_shape(prec, d, n_dir[d]);
+        const bool line64 = prec == NPB_FP64 && shape[d].kind == 3;  // no TMA: direct global access
+        if (shape[d].kind >= 1 && !tma[d] && !line64) shape[d] = default_sweep_shape(prec, d, n_dir[d]);
     }
     cudaEvent_t ev{};
     int rc;
@@ -795,6 +826,8 @@ int npb::step_legs(npb_ctx *ctx, const LegRef *refs, int n, const LegDev *d_tabl
                 else if (shape[d].kind == 2) CU(launch_sweep_inner(d, P, refs[c0].g->tma_g[d], flags, shape[d], ctx->sm_count, st));
                 else CU(launch_sweep_tma(d, P, refs[c0].g->tma_g[d], flags, shape[d], ctx->sm_count, st));
             }
+        } else if (prec == NPB_FP64 && shape[d].kind == 3) {
+            CU(launch_sweep_line64(d, d_table, n, nx, ny, nz, flags, st));
         } else {
             CU(launch_sweep(prec, d, d_table, n, nx, ny, nz, flags, shape[d], st));
         }

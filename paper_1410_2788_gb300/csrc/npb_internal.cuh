@@ -57,6 +57,11 @@ struct LegDev {
     // carry the leg's r*eps outside the molecule (r*eps_in for vacuum legs), j = 1 .. ceil((n-2)/2);
     // the line-per-thread-pair sweeps use them on tiles of constant coefficients (null: no table)
     const float2 *line_tab[3];
+    // FP64 legs, per direction: the line-per-thread-pair solver's multipliers m of every node (the
+    // state's layout), computed once per leg from eps and r (null: not in use); and the node mask
+    // line-major along each direction ([0]: the x rows of `mask`; null with `mask`)
+    double *fac[3];
+    const uint32_t *lmask[3];
 };
 
 // Entries of one direction's multiplier table (n <= 288 nodes per line).

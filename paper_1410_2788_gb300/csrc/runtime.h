@@ -153,6 +153,8 @@ struct npb_grid {
     CUtensorMap tma_aux[2][3][4];  // [x | y][variant][slot]
     bool tma_aux_built = false;
     double *d_vac_fft = nullptr;  // phi_0^FFT of Eq. (deltaG2), padded FP64 (fft_vacuum.cu)
+    double *d_fac[4][3] = {};     // FP64 legs: Thomas multipliers per slot and direction (sweep_line64.cu)
+    bool fac_valid = false;       // they match the current legs and mask
     bool vac_fft_valid = false;
     int vac_fft_kind = -1;         // face flavour it was built from (0 FP64 pairs, 1 FP32 pairs)
     int last_richardson = 1;       // flags of the last npb_energy (for the recovered potential)
@@ -205,7 +207,10 @@ int grid_states(Grid *g, int prec, cudaStream_t st);
 int grid_prepare(Grid *g, const npb_opts *o, cudaStream_t st);
 LegDev make_leg(const Grid *g, int leg, const npb_opts *o);
 SweepShape shape_for(Ctx *ctx, int prec, int dir, int n);
-SweepShape usable_shape(SweepShape s, int dir, int n, bool tables, int flags);
+SweepShape usable_shape(SweepShape s, int dir, int n, bool tables, int flags, int prec = NPB_FP32_SWEEP);
+cudaError_t launch_line64_factors(int dir, const LegDev *legs, int n_legs, int nx, int ny, int nz, cudaStream_t st);
+cudaError_t launch_sweep_line64(int dir, const LegDev *legs, int n_legs, int nx, int ny, int nz, int flags,
+                                cudaStream_t st);
 struct LegRef {
     Grid *g;
     int slot;

@@ -1,0 +1,217 @@
+// sweep_line64.cu -- FP64 LOD line solves, one grid line per pair of threads, with the Thomas
+// multipliers computed once per leg (solver kind 3 for the plain FP64 path).
+//
+// The implicit-Euler system of one LOD direction (Eqs. LODIE1_2-LODIE1_4, eps at half points) is
+// solved by the Thomas recurrence of Sec. 3.1, from both ends of the line at once: the lower thread
+// eliminates rows 1 .. p downwards (p = ceil(N/2), N = n-2), the upper thread rows N .. p+1 upwards,
+// the two middle rows are solved together, and each thread back-substitutes its half.  The
+// multipliers m_k = 1/(1 + e_lo + e_hi - e_lo cp_{k-1}) (downwards; mirrored upwards) depend only on
+// eps and r = tau/h^2, not on u, so they are computed once per leg and direction (k_line64_factors)
+// and read back at every step: a row then costs two FP64 multiply-adds on the way down and two on the
+// way up, instead of a division and the segmented elimination's bookkeeping.  GB300's FP64 units run
+// at about 1/64 of its FP32 rate, so the plain FP64 path is bound by them; fewer FP64 operations per
+// node is what speeds it up.  u is read and written in place in global memory: for y and z the 32
+// lines of a warp are x-adjacent (coalesced rows), for x each lane walks its own row.
+//
+// Fused stages (flags): S (LODIE2) and N (LODIE1) on the x sweep's loaded rows, N (LODIE2) on the z
+// sweep's results.
+#include <algorithm>
+
+#include "npb_internal.cuh"
+#include "sweep_kernel.cuh"
+
+namespace npb {
+
+constexpr int kL64Lines = 32;
+
+struct L64Line {
+    int64_t base, step;    // element of row g: base + g * step
+    int64_t mbase;         // first mask word of the line
+    bool active;
+};
+
+template <int DIR>
+__device__ __forceinline__ L64Line l64_line(const LegDev &lg, int a, int c, int lane) {
+    L64Line L;
+    const int64_t pitch = lg.pitch, ny = lg.ny;
+    if (DIR == DIR_X) {  // line (y, z), y = 1 + a*32 + lane, z = c
+        const int y = 1 + a * kL64Lines + lane;
+        L.active = y <= lg.ny - 2;
+        L.base = ((int64_t)c * ny + y) * pitch;
+        L.step = 1;
+        L.mbase = ((int64_t)c * ny + y) * mask_words_per_row(lg.pitch);
+    } else {  // line (x, c): x = a*32 + lane; c = z (y sweep) or y (z sweep)
+        const int x = a * kL64Lines + lane;
+        L.active = x >= 1 && x <= lg.nx - 2;
+        if (DIR == DIR_Y) {
+            L.base = (int64_t)c * ny * pitch + x;
+            L.step = pitch;
+            L.mbase = ((int64_t)c * lg.nx + x) * line_words(lg.ny);
+        } else {
+            L.base = (int64_t)c * pitch + x;
+            L.step = ny * pitch;
+            L.mbase = ((int64_t)c * lg.nx + x) * line_words(lg.nz);
+        }
+    }
+    return L;
+}
+
+// r*eps at the half point g + 1/2 from the node bits of g and g + 1.
+__device__ __forceinline__ double l64_e(const double *rE, uint32_t b0, uint32_t b1) {
+    return (b0 & b1) ? rE[2] : ((b0 | b1) ? rE[1] : rE[0]);
+}
+
+// Node bit g of a line (1 = inside); no mask: every node inside (the vacuum legs' constant eps_in).
+struct L64Bits {
+    const uint32_t *w;
+    int cur;
+    uint32_t word;
+    __device__ __forceinline__ uint32_t operator()(int g) {
+        if (!w) return 1u;
+        if ((g >> 5) != cur) {
+            cur = g >> 5;
+            word = w[cur];
+        }
+        return (word >> (g & 31)) & 1u;
+    }
+};
+
+// Multipliers of every line of leg blockIdx.z along DIR into lg.fac[DIR].
+template <int DIR>
+__global__ void __launch_bounds__(2 * kL64Lines) k_line64_factors(const LegDev *__restrict__ legs, int tiles_a) {
+    const LegDev &lg = legs[blockIdx.z];
+    const int lane = threadIdx.x & 31;
+    const bool upper = threadIdx.x >= 32;
+    const L64Line L = l64_line<DIR>(lg, blockIdx.x, 1 + blockIdx.y, lane);
+    if (!L.active) return;
+    const int n = DIR == DIR_X ? lg.nx : (DIR == DIR_Y ? lg.ny : lg.nz);
+    const int N = n - 2, p = (N + 1) >> 1;
+    double *f = lg.fac[DIR] + L.base;
+    L64Bits bit{lg.lmask[DIR] ? lg.lmask[DIR] + L.mbase : nullptr, -1, 0u};
+    if (!upper) {
+        double cp = 0.0, el = l64_e(lg.rE, bit(0), bit(1));
+        for (int k = 1; k <= p; ++k) {
+            const double er = l64_e(lg.rE, bit(k), bit(k + 1));
+            const double m = 1.0 / (1.0 + el + er - el * cp);
+            f[k * L.step] = m;
+            cp = er * m;
+            el = er;
+        }
+    } else {
+        double aq = 0.0, er = l64_e(lg.rE, bit(N), bit(N + 1));
+        for (int k = N; k > p; --k) {
+            const double el = l64_e(lg.rE, bit(k - 1), bit(k));
+            const double m = 1.0 / (1.0 + el + er - er * aq);
+            f[k * L.step] = m;
+            aq = el * m;
+            er = el;
+        }
+    }
+}
+
+template <int DIR>
+__global__ void __launch_bounds__(2 * kL64Lines) k_line64_sweep(const LegDev *__restrict__ legs, int flags) {
+    __shared__ double2 xbuf[2 * kL64Lines];
+    const LegDev &lg = legs[blockIdx.z];
+    const int lane = threadIdx.x & 31;
+    const bool upper = threadIdx.x >= 32;
+    const int c = 1 + blockIdx.y;
+    const L64Line L = l64_line<DIR>(lg, blockIdx.x, c, lane);
+    const int n = DIR == DIR_X ? lg.nx : (DIR == DIR_Y ? lg.ny : lg.nz);
+    const int N = n - 2, p = (N + 1) >> 1;
+    double *u = static_cast<double *>(lg.u) + L.base;
+    const double *f = lg.fac[DIR] + L.base;
+    const int64_t st = L.step;
+    L64Bits bit{lg.lmask[DIR] ? lg.lmask[DIR] + L.mbase : nullptr, -1, 0u};
+    const bool nl_on = lg.nl_on != 0;
+    const bool pre_nl = DIR == DIR_X && (flags & FUSE_PRE_NL) && nl_on;
+    const bool post_nl = DIR == DIR_Z && (flags & FUSE_POST_NL) && nl_on;
+    const bool pre_src = DIR == DIR_X && (flags & FUSE_PRE_SRC);
+    auto flow = [&](double v) { return nl_flow_leg(v, lg.nl_q, lg.nl_omq); };
+
+    double dv = 0.0, cv = 0.0;  // (dp_p, cp_p) of the lower thread, (dq_{p+1}, aq_{p+1}) of the upper
+    if (L.active) {
+        // the rows this thread owns: 1 .. p (lower) or p+1 .. N (upper)
+        const int r0 = upper ? p + 1 : 1, r1 = upper ? N : p;
+        if (pre_nl)  // LODIE1's N at the solvent nodes outside the molecule, before the solve
+            for (int k = r0; k <= r1; ++k)
+                if (!bit(k)) u[k * st] = flow(u[k * st]);
+        if (pre_src) {  // LODIE2's S: tau Q at this half's charge nodes of the line (y, z = c)
+            const int ln = c * lg.ny + (1 + blockIdx.x * kL64Lines + lane);
+            const int b = lg.line_begin[ln], e = b + lg.line_count[ln];
+            for (int q = b; q < e; ++q) {
+                const int x = lg.ent_x[q];
+                if (x >= r0 && x <= r1) u[x * st] += lg.src * lg.ent_qt[q];
+            }
+        }
+        if (!upper) {
+            dv = u[0];  // the face u_0 enters as e_{1/2} dp_0
+            double el = l64_e(lg.rE, bit(0), bit(1));
+            for (int k = 1; k <= p; ++k) {
+                const double er = l64_e(lg.rE, bit(k), bit(k + 1));
+                const double m = f[k * st];
+                dv = fma(el, dv, u[k * st]) * m;
+                u[k * st] = dv;
+                cv = er * m;
+                el = er;
+            }
+        } else {
+            dv = u[(N + 1) * st];  // u_{n-1}
+            double er = l64_e(lg.rE, bit(N), bit(N + 1));
+            for (int k = N; k > p; --k) {
+                const double el = l64_e(lg.rE, bit(k - 1), bit(k));
+                const double m = f[k * st];
+                dv = fma(er, dv, u[k * st]) * m;
+                u[k * st] = dv;
+                cv = el * m;
+                er = el;
+            }
+        }
+    }
+    xbuf[threadIdx.x] = make_double2(dv, cv);
+    __syncthreads();
+    if (!L.active) return;
+    const double2 lo = xbuf[lane], hi = xbuf[kL64Lines + lane];
+    const double vp = (lo.x + lo.y * hi.x) / (1.0 - lo.y * hi.y);
+    if (!upper) {
+        double v = vp;
+        u[p * st] = (post_nl && !bit(p)) ? flow(v) : v;
+        for (int k = p - 1; k >= 1; --k) {
+            const double er = l64_e(lg.rE, bit(k), bit(k + 1));
+            v = fma(er * f[k * st], v, u[k * st]);
+            u[k * st] = (post_nl && !bit(k)) ? flow(v) : v;
+        }
+    } else if (p < N) {
+        double v = fma(hi.y, vp, hi.x);
+        u[(p + 1) * st] = (post_nl && !bit(p + 1)) ? flow(v) : v;
+        for (int k = p + 2; k <= N; ++k) {
+            const double el = l64_e(lg.rE, bit(k - 1), bit(k));
+            v = fma(el * f[k * st], v, u[k * st]);
+            u[k * st] = (post_nl && !bit(k)) ? flow(v) : v;
+        }
+    }
+}
+
+static dim3 l64_grid(int dir, int n_legs, int nx, int ny, int nz) {
+    if (dir == DIR_X) return dim3((ny - 2 + kL64Lines - 1) / kL64Lines, nz - 2, n_legs);
+    return dim3((nx - 1 + kL64Lines - 1) / kL64Lines, dir == DIR_Y ? nz - 2 : ny - 2, n_legs);
+}
+
+cudaError_t launch_line64_factors(int dir, const LegDev *legs, int n_legs, int nx, int ny, int nz, cudaStream_t st) {
+    const dim3 g = l64_grid(dir, n_legs, nx, ny, nz);
+    if (dir == DIR_X) k_line64_factors<DIR_X><<<g, 2 * kL64Lines, 0, st>>>(legs, g.x);
+    else if (dir == DIR_Y) k_line64_factors<DIR_Y><<<g, 2 * kL64Lines, 0, st>>>(legs, g.x);
+    else k_line64_factors<DIR_Z><<<g, 2 * kL64Lines, 0, st>>>(legs, g.x);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_line64(int dir, const LegDev *legs, int n_legs, int nx, int ny, int nz, int flags,
+                                cudaStream_t st) {
+    const dim3 g = l64_grid(dir, n_legs, nx, ny, nz);
+    if (dir == DIR_X) k_line64_sweep<DIR_X><<<g, 2 * kL64Lines, 0, st>>>(legs, flags);
+    else if (dir == DIR_Y) k_line64_sweep<DIR_Y><<<g, 2 * kL64Lines, 0, st>>>(legs, flags);
+    else k_line64_sweep<DIR_Z><<<g, 2 * kL64Lines, 0, st>>>(legs, flags);
+    return cudaGetLastError();
+}
+
+}  // namespace npb

@@ -36,6 +36,7 @@ extern "C" int npb_autotune(npb_grid *g, const npb_opts *o, int32_t reps, char *
             ns += inner_shapes(d, shapes + ns, 96 - ns);
             ns += line_shapes(d, shapes + ns, 96 - ns);
         }
+        if (prec == NPB_FP64 && ns < 96) shapes[ns++] = SweepShape{32, 2, 1, 3};  // Thomas per line
         SweepShape best{0, 0, 0, 0};
         float best_ms = 1e30f;
         for (int i = 0; i < ns; ++i) {
@@ -90,6 +91,8 @@ extern "C" int npb_tune_set(npb_ctx *ctx, int32_t precision, int32_t dir, int32_
     bool found = false;
     if (kind == 0) {
         found = sweep_shape_available(precision, s);
+    } else if (precision == NPB_FP64) {
+        found = kind == 3 && tx == 32 && seg == 2 && len == 1;  // Thomas per line, multipliers once per leg
     } else if (precision == NPB_FP32_SWEEP) {
         const int k = kind == 1 ? tma_shapes(dir, t, 32) : (kind == 2 ? inner_shapes(dir, t, 32) : line_shapes(dir, t, 32));
         for (int i = 0; i < k && !found; ++i) found = t[i].tx == tx && t[i].seg == seg && t[i].len == len;

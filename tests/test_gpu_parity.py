@@ -417,12 +417,14 @@ CLASSIC_SHAPES = [(16, 2, 17), (16, 4, 9), (16, 4, 17), (16, 8, 9), (16, 8, 13),
 @pytest.mark.parametrize("prec", [0, 1])
 def test_every_solver_shape_matches_oracle(npb, O, prec):
     """Each instantiated line-solver shape (Thomas/PCR split, lines per block, TMA pipeline or
-    not) gives the oracle's answer on a 65^3 molecule (RE+V, 6 steps)."""
+    not, Thomas per line) gives the oracle's answer on a 65^3 molecule (RE+V, 6 steps)."""
     p = I.random_walk_molecule(120, 65, 0.5, seed=I.SEED_BASE + 72)
     n = 6
     ref_dg, ref_legs, _ = O.energy(p, 10.0, n, return_legs=True)
     tol = 1e-10 if prec == 0 else 1e-4
     shapes = [(d, 0, s) for d in range(3) for s in CLASSIC_SHAPES]
+    if prec == 0:  # FP64 Thomas per line with the multipliers computed once per leg (the FP64 default)
+        shapes += [(d, 3, (32, 2, 1)) for d in range(3)]
     if prec == 1:
         shapes += [(d, 1, s) for d in range(3) for s in TMA_SHAPES[min(d, 1)]]
         shapes += [(d, 2, s) for d in range(3) for s in INNER_SHAPES[min(d, 1)]]
