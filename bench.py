@@ -419,9 +419,15 @@ def serving_run(npb, seconds: float, rate: float = 50.0, fifo_requests: int = 50
     return out
 
 
-def _kernel_source_hash() -> str:
+# The sources of the FP32 interior-row sweeps (the kernels whose DRAM traffic profiles/ncu_traffic.json
+# records) and of the FP64 line sweeps.
+FP32_SWEEP_SOURCES = ("sweep_kernel.cuh", "sweep_tma.cuh", "sweep_inner.cuh", "sweep_inner_launch.cuh")
+FP64_SWEEP_SOURCES = ("sweep_kernel.cuh", "sweep_line64.cu")
+
+
+def _kernel_source_hash(files=FP32_SWEEP_SOURCES) -> str:
     h = hashlib.sha256()
-    for f in ("sweep_kernel.cuh", "sweep_tma.cuh", "sweep_inner.cuh", "sweep_inner_launch.cuh", "sweep_line.cuh"):
+    for f in files:
         h.update(open(os.path.join(ROOT, "paper_1410_2788_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -446,21 +452,24 @@ def roofline_traffic(kernel: str, workload: str):
     return e.get("dram_bytes_per_launch")
 
 
-def fp64_roofline(point_steps_per_s, dfma_per_s, ddiv_per_s):
-    """The plain FP64 path against the FP64 units: FP64 flops per interior point-step counted by ncu
-    on the FP64 sweeps (profiles/ncu_fp64_ops.json, when it matches the kernel source) times the
-    measured point-steps/s, over twice the measured FMA rate (npb_measure_fp64).  The whole step is
-    timed, set-up included, so the fraction understates the sweeps' own."""
-    out = {"bound": "alu", "unit": "GFLOP/s", "peak": 2 * dfma_per_s / 1e9, "peak_source": "measured",
-           "measured_dfma_per_s": dfma_per_s, "measured_ddiv_per_s": ddiv_per_s}
+def fp64_roofline(point_steps_per_s, dfma_per_s, ddiv_per_s, peak, peak_kind):
+    """The plain FP64 path's sweeps against HBM: the FP64 Thomas-per-line kernel moves 48 B per
+    interior node per sweep (u read and written, the forward result written and read back, the
+    precomputed multiplier read on the way down and on the way up), 144 B per point-step.  The whole
+    step is timed, set-up (the FP64 faces) included, so the fraction understates the sweeps' own.  The
+    FP64 units' measured rates (npb_measure_fp64) and, when profiles/ncu_fp64_ops.json matches the
+    kernel source, the FP64 operations per point-step counted by ncu go beside it."""
+    ach = 144.0 * point_steps_per_s / 1e9
+    out = {"bound": "hbm", "unit": "GB/s", "achieved": ach, "peak": peak, "frac": ach / peak,
+           "peak_source": peak_kind, "alg_bytes_per_point_step": 144,
+           "measured_fp64_fma_per_s": dfma_per_s, "measured_fp64_div_per_s": ddiv_per_s}
     path = os.path.join(ROOT, "profiles", "ncu_fp64_ops.json")
     e = json.load(open(path)).get("protein_1k") if os.path.exists(path) else None
-    if e and e.get("source_hash") == _kernel_source_hash():
+    if e and e.get("source_hash") == _kernel_source_hash(FP64_SWEEP_SOURCES):
         flops = sum(e["flops_per_node_sweep"].values())
-        out.update(achieved=flops * point_steps_per_s / 1e9, frac=flops * point_steps_per_s / (2 * dfma_per_s),
-                   flops_per_point_step=flops, fp64_pipe_busy_ncu=e["fp64_pipe_busy"])
-    else:
-        out.update(achieved=None, frac=None)
+        out["fp64"] = {"flops_per_point_step": flops, "achieved_gflops": flops * point_steps_per_s / 1e9,
+                       "peak_gflops": 2 * dfma_per_s / 1e9, "frac": flops * point_steps_per_s / (2 * dfma_per_s),
+                       "fp64_pipe_busy_ncu": e.get("fp64_pipe_busy")}
     return out
 
 
@@ -697,7 +706,7 @@ def run_ours(args):
         "solves_per_s": args.steps * world / total_s,
         "fp64_path": dict({"value": u64 / t64 / 1e6, "unit": UNIT, "ms_per_step": 1e3 * t64 / k64,
                            "solves_per_s": k64 * world / t64, "dG_kcal_mol": dg64},
-                          roofline=fp64_roofline(u64 / t64, dfma_s, ddiv_s)),
+                          roofline=fp64_roofline(u64 / t64, dfma_s, ddiv_s, *measured_peaks())),
         "error_vs_oracle": errors,
         "wall_s_timed_region": wall,
         "roofline": roofline,

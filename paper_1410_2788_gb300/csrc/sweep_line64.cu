@@ -23,6 +23,7 @@
 namespace npb {
 
 constexpr int kL64Lines = 32;
+constexpr int kL64Chunk = 8;  // rows whose loads are issued together
 
 struct L64Line {
     int64_t base, step;    // element of row g: base + g * step
@@ -144,27 +145,53 @@ __global__ void __launch_bounds__(2 * kL64Lines) k_line64_sweep(const LegDev *__
                 if (x >= r0 && x <= r1) u[x * st] += lg.src * lg.ent_qt[q];
             }
         }
+        // rows in chunks of kL64Chunk: every chunk's loads are issued before its dependent
+        // recurrence, so the global-memory latency overlaps (each lane of an x sweep walks its own row)
         if (!upper) {
             dv = u[0];  // the face u_0 enters as e_{1/2} dp_0
             double el = l64_e(lg.rE, bit(0), bit(1));
-            for (int k = 1; k <= p; ++k) {
-                const double er = l64_e(lg.rE, bit(k), bit(k + 1));
-                const double m = f[k * st];
-                dv = fma(el, dv, u[k * st]) * m;
-                u[k * st] = dv;
-                cv = er * m;
-                el = er;
+            for (int k0 = 1; k0 <= p; k0 += kL64Chunk) {
+                const int nk = min(kL64Chunk, p - k0 + 1);
+                double w[kL64Chunk], m[kL64Chunk];
+#pragma unroll
+                for (int j = 0; j < kL64Chunk; ++j)
+                    if (j < nk) {
+                        w[j] = u[(k0 + j) * st];
+                        m[j] = f[(k0 + j) * st];
+                    }
+#pragma unroll
+                for (int j = 0; j < kL64Chunk; ++j)
+                    if (j < nk) {
+                        const int k = k0 + j;
+                        const double er = l64_e(lg.rE, bit(k), bit(k + 1));
+                        dv = fma(el, dv, w[j]) * m[j];
+                        u[k * st] = dv;
+                        cv = er * m[j];
+                        el = er;
+                    }
             }
         } else {
             dv = u[(N + 1) * st];  // u_{n-1}
             double er = l64_e(lg.rE, bit(N), bit(N + 1));
-            for (int k = N; k > p; --k) {
-                const double el = l64_e(lg.rE, bit(k - 1), bit(k));
-                const double m = f[k * st];
-                dv = fma(er, dv, u[k * st]) * m;
-                u[k * st] = dv;
-                cv = el * m;
-                er = el;
+            for (int k0 = N; k0 > p; k0 -= kL64Chunk) {
+                const int nk = min(kL64Chunk, k0 - p);
+                double w[kL64Chunk], m[kL64Chunk];
+#pragma unroll
+                for (int j = 0; j < kL64Chunk; ++j)
+                    if (j < nk) {
+                        w[j] = u[(k0 - j) * st];
+                        m[j] = f[(k0 - j) * st];
+                    }
+#pragma unroll
+                for (int j = 0; j < kL64Chunk; ++j)
+                    if (j < nk) {
+                        const int k = k0 - j;
+                        const double el = l64_e(lg.rE, bit(k - 1), bit(k));
+                        dv = fma(er, dv, w[j]) * m[j];
+                        u[k * st] = dv;
+                        cv = el * m[j];
+                        er = el;
+                    }
             }
         }
     }
@@ -176,18 +203,44 @@ __global__ void __launch_bounds__(2 * kL64Lines) k_line64_sweep(const LegDev *__
     if (!upper) {
         double v = vp;
         u[p * st] = (post_nl && !bit(p)) ? flow(v) : v;
-        for (int k = p - 1; k >= 1; --k) {
-            const double er = l64_e(lg.rE, bit(k), bit(k + 1));
-            v = fma(er * f[k * st], v, u[k * st]);
-            u[k * st] = (post_nl && !bit(k)) ? flow(v) : v;
+        for (int k0 = p - 1; k0 >= 1; k0 -= kL64Chunk) {
+            const int nk = min(kL64Chunk, k0);
+            double w[kL64Chunk], m[kL64Chunk];
+#pragma unroll
+            for (int j = 0; j < kL64Chunk; ++j)
+                if (j < nk) {
+                    w[j] = u[(k0 - j) * st];
+                    m[j] = f[(k0 - j) * st];
+                }
+#pragma unroll
+            for (int j = 0; j < kL64Chunk; ++j)
+                if (j < nk) {
+                    const int k = k0 - j;
+                    const double er = l64_e(lg.rE, bit(k), bit(k + 1));
+                    v = fma(er * m[j], v, w[j]);
+                    u[k * st] = (post_nl && !bit(k)) ? flow(v) : v;
+                }
         }
     } else if (p < N) {
         double v = fma(hi.y, vp, hi.x);
         u[(p + 1) * st] = (post_nl && !bit(p + 1)) ? flow(v) : v;
-        for (int k = p + 2; k <= N; ++k) {
-            const double el = l64_e(lg.rE, bit(k - 1), bit(k));
-            v = fma(el * f[k * st], v, u[k * st]);
-            u[k * st] = (post_nl && !bit(k)) ? flow(v) : v;
+        for (int k0 = p + 2; k0 <= N; k0 += kL64Chunk) {
+            const int nk = min(kL64Chunk, N - k0 + 1);
+            double w[kL64Chunk], m[kL64Chunk];
+#pragma unroll
+            for (int j = 0; j < kL64Chunk; ++j)
+                if (j < nk) {
+                    w[j] = u[(k0 + j) * st];
+                    m[j] = f[(k0 + j) * st];
+                }
+#pragma unroll
+            for (int j = 0; j < kL64Chunk; ++j)
+                if (j < nk) {
+                    const int k = k0 + j;
+                    const double el = l64_e(lg.rE, bit(k - 1), bit(k));
+                    v = fma(el * m[j], v, w[j]);
+                    u[k * st] = (post_nl && !bit(k)) ? flow(v) : v;
+                }
         }
     }
 }
