@@ -958,9 +958,15 @@ extern "C" int npb_energy(npb_grid *g, const npb_opts *o, double *dG) {
     g->last_vacuum_lod = o->vacuum_recovery ? 1 : 0;
     const bool use_graph = !ctx->prof.enabled && st != nullptr && ctx->use_graphs && ctx->probe_cycles == 0;
     if (use_graph) {
-        char key[256];
-        snprintf(key, sizeof key, "%d/%d/%d/%d/%d/%d/%s", o->precision, o->scheme, o->richardson, o->n_steps,
-                 o->eps_mode, o->vacuum_recovery, g->legs_key[o->precision].c_str());
+        // the line-solver shapes are part of the key: a shape pinned after a capture takes effect
+        const int nd[3] = {g->geo.nx, g->geo.ny, g->geo.nz};
+        SweepShape sh[3];
+        for (int d = 0; d < 3; ++d) sh[d] = shape_for(ctx, o->precision, d, nd[d]);
+        char key[384];
+        snprintf(key, sizeof key, "%d/%d/%d/%d/%d/%d/%d.%d.%d.%d/%d.%d.%d.%d/%d.%d.%d.%d/%s", o->precision, o->scheme,
+                 o->richardson, o->n_steps, o->eps_mode, o->vacuum_recovery, sh[0].kind, sh[0].tx, sh[0].seg,
+                 sh[0].len, sh[1].kind, sh[1].tx, sh[1].seg, sh[1].len, sh[2].kind, sh[2].tx, sh[2].seg, sh[2].len,
+                 g->legs_key[o->precision].c_str());
         GraphCache *hit = nullptr;
         for (auto &c : g->graphs)
             if (c.key == key && c.stream == st) hit = &c;

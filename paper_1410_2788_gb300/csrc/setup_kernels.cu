@@ -362,101 +362,6 @@ __global__ void k_boundary_pair_f32(GridGeom g, const double *__restrict__ xyz, 
     }
 }
 
-// The same FP32 pair terms with each thread on kRowBlock adjacent nodes of one face row: FT = 0
-// the z faces (rows along x, fixed y and z), 1 the y faces (rows along x, fixed y and z), 2 the x
-// faces (rows along y, fixed x and z).  Per atom the two fixed coordinate differences and the sum
-// of their squares are shared by the row's nodes, so a pair term costs one subtraction and one
-// fused multiply-add for its squared distance instead of six operations.
-constexpr int kRowBlock = 4;
-
-template <int FT>
-__global__ void k_boundary_rows_f32(GridGeom g, const double *__restrict__ xyz, const double *__restrict__ q,
-                                    int n_atoms, double eps_s, double kbar, double eps_v, double *__restrict__ out_s,
-                                    double *__restrict__ out_v) {
-    __shared__ float4 sa[kAtomChunk];
-    const int nx = g.nx, ny = g.ny, nz = g.nz;
-    const int64_t A = (int64_t)nx * ny, B = (int64_t)nx * (nz - 2), Cc = (int64_t)(ny - 2) * (nz - 2);
-    const int len = FT == 2 ? ny - 2 : nx;                  // nodes per row
-    const int rows = FT == 0 ? ny : nz - 2;                 // rows per face
-    const int chunks = (len + kRowBlock - 1) / kRowBlock;
-    const int64_t items = 2LL * rows * chunks;
-    const int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool live = it < items;
-    const int side = live ? (int)(it / ((int64_t)rows * chunks)) : 0;
-    const int64_t rr = live ? it % ((int64_t)rows * chunks) : 0;
-    const int row = (int)(rr / chunks), ch = (int)(rr % chunks);
-    // fixed coordinates (fu, fv) and the first node of the row segment along the fast axis
-    int i0 = 0, j0 = 0, k0 = 0;
-    int64_t f0 = 0;  // compact face index of the first node; the next nodes follow at +1
-    if (FT == 0) {
-        k0 = side ? nz - 1 : 0;
-        j0 = row;
-        i0 = ch * kRowBlock;
-        f0 = (side ? A : 0) + (int64_t)j0 * nx + i0;
-    } else if (FT == 1) {
-        j0 = side ? ny - 1 : 0;
-        k0 = 1 + row;
-        i0 = ch * kRowBlock;
-        f0 = 2 * A + (side ? B : 0) + (int64_t)row * nx + i0;
-    } else {
-        i0 = side ? nx - 1 : 0;
-        k0 = 1 + row;
-        j0 = 1 + ch * kRowBlock;
-        f0 = 2 * A + 2 * B + (side ? Cc : 0) + (int64_t)row * (ny - 2) + (j0 - 1);
-    }
-    const int n_here = live ? min(kRowBlock, len - ch * kRowBlock) : 0;
-    // positions relative to the grid origin keep FP32 resolution near 1e-5 A
-    float w[kRowBlock];  // the fast coordinate of each node
-#pragma unroll
-    for (int r = 0; r < kRowBlock; ++r) w[r] = FT == 2 ? (float)((j0 + r) * g.h) : (float)((i0 + r) * g.h);
-    const float fu = FT == 2 ? (float)(i0 * g.h) : (float)(j0 * g.h);  // fixed: x (FT 2) or y
-    const float fv = (float)(k0 * g.h);                                 // fixed: z
-    const float c = (float)(-kbar / sqrt(eps_s) * 1.4426950408889634);
-    const bool coulomb = kbar == 0.0;
-    double ss[kRowBlock], sv[kRowBlock];
-#pragma unroll
-    for (int r = 0; r < kRowBlock; ++r) ss[r] = sv[r] = 0.0;
-    for (int a0 = 0; a0 < n_atoms; a0 += kAtomChunk) {
-        __syncthreads();
-        for (int t = threadIdx.x; t < kAtomChunk && a0 + t < n_atoms; t += blockDim.x) {
-            // (fast, fixed u, fixed v, q) of the atom in this face type's axes
-            const float ax = (float)(xyz[3 * (a0 + t)] - g.ox), ay = (float)(xyz[3 * (a0 + t) + 1] - g.oy);
-            const float az = (float)(xyz[3 * (a0 + t) + 2] - g.oz);
-            sa[t] = FT == 2 ? make_float4(ay, ax, az, (float)q[a0 + t]) : make_float4(ax, ay, az, (float)q[a0 + t]);
-        }
-        __syncthreads();
-        const int na = min(kAtomChunk, n_atoms - a0);
-        float ps[kRowBlock], pv[kRowBlock];
-#pragma unroll
-        for (int r = 0; r < kRowBlock; ++r) ps[r] = pv[r] = 0.f;
-        for (int t = 0; t < na; ++t) {
-            const float4 P = sa[t];
-            const float du = fu - P.y, dv = fv - P.z;
-            const float uv2 = fmaf(du, du, dv * dv);
-#pragma unroll
-            for (int r = 0; r < kRowBlock; ++r) {
-                const float dw = w[r] - P.x;
-                const float d2 = fmaf(dw, dw, uv2);
-                const float id = rsqrtf(d2);
-                const float qi = P.w * id;
-                pv[r] += qi;
-                if (!coulomb) ps[r] = fmaf(qi, ex2_approx(c * (d2 * id)), ps[r]);
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < kRowBlock; ++r) {
-            ss[r] += (double)(coulomb ? pv[r] : ps[r]);
-            sv[r] += (double)pv[r];
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < kRowBlock; ++r)
-        if (r < n_here) {
-            out_s[f0 + r] = kBjerrum / eps_s * ss[r];
-            out_v[f0 + r] = kBjerrum / eps_v * sv[r];
-        }
-}
-
 // Both media's faces in one pass, FP64 pair terms (the parity path): the two sums share the
 // distance, taken as d^2 * rsqrt(d^2), and 1/d = rsqrt(d^2); only the solvent's screening needs its
 // exponential.  Each thread holds kFaceBlock face nodes; the atoms are summed in index order.
@@ -638,18 +543,9 @@ cudaError_t setup_boundary_pair(const GridGeom &g, const double *xyz, const doub
     if (fp64)
         k_boundary_pair_f64<<<blocks_for(nf, (int64_t)t * kFaceBlock), t, 0, st>>>(g, xyz, q, n_atoms, eps_out, kbar,
                                                                                    eps_in, out_s, out_v);
-    else {
-        // one launch per face type, each thread on kRowBlock adjacent nodes of a row
-        const int64_t cz = (g.nx + kRowBlock - 1) / kRowBlock, cx = (g.ny - 2 + kRowBlock - 1) / kRowBlock;
-        const int64_t n0 = 2LL * g.ny * cz, n1 = 2LL * (g.nz - 2) * cz, n2 = 2LL * (g.nz - 2) * cx;
-        k_boundary_rows_f32<0><<<blocks_for(n0, t), t, 0, st>>>(g, xyz, q, n_atoms, eps_out, kbar, eps_in, out_s, out_v);
-        if (n1 > 0)
-            k_boundary_rows_f32<1><<<blocks_for(n1, t), t, 0, st>>>(g, xyz, q, n_atoms, eps_out, kbar, eps_in, out_s,
-                                                                    out_v);
-        if (n2 > 0)
-            k_boundary_rows_f32<2><<<blocks_for(n2, t), t, 0, st>>>(g, xyz, q, n_atoms, eps_out, kbar, eps_in, out_s,
-                                                                    out_v);
-    }
+    else
+        k_boundary_pair_f32<<<blocks_for(nf, (int64_t)t * kFaceBlock), t, 0, st>>>(g, xyz, q, n_atoms, eps_out, kbar,
+                                                                                   eps_in, out_s, out_v);
     return cudaGetLastError();
 }
 

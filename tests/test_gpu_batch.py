@@ -130,3 +130,37 @@ def test_batch_with_tuned_shapes_and_tuning_cache(npb, O, tmp_path):
     for p, v in zip(mols[:2], batch[:2]):
         ref = O.energy(p, 10.0, 6)
         assert abs(v - ref) <= 1e-4 * abs(ref), (v, ref)
+
+
+def test_shape_pinned_after_a_captured_solve_takes_effect(npb):
+    """A solve that came back (and so replays a captured CUDA graph) runs the line-solver shape
+    pinned since: its energy equals bit for bit that of a fresh context with the new shape pinned
+    from the start, for each of several x shapes in turn."""
+    p = _mols()[0]
+    nx = p.n[0]
+    o = npb.make_opts(0.4, 0.04, 6, precision=1)
+    seq = [(2, 8, 24, 11), (2, 8, 16, 17), (2, 8, 8, 9), (2, 8, 20, 13)]
+    fresh = []
+    for sh in seq:
+        c = npb.npb_ctx_create(0, 0)
+        try:
+            npb.npb_tune_set(c, 1, 0, nx, *sh)
+            g = npb.npb_grid_create(c, p)
+            try:
+                fresh.append(npb.npb_energy(g, o))
+            finally:
+                npb.npb_grid_destroy(g)
+        finally:
+            npb.npb_ctx_destroy(c)
+    c = npb.npb_ctx_create(0, 0)
+    try:
+        g = npb.npb_grid_create(c, p)
+        try:
+            for sh, want in zip(seq, fresh):
+                npb.npb_tune_set(c, 1, 0, nx, *sh)
+                got = [npb.npb_energy(g, o) for _ in range(3)]  # direct, captured, replayed
+                assert got == [want] * 3, (sh, got, want)
+        finally:
+            npb.npb_grid_destroy(g)
+    finally:
+        npb.npb_ctx_destroy(c)
