@@ -12,10 +12,12 @@ namespace npb {
 
 // (SEG, L) pairs for tiles of 8 lines (SEG a multiple of 4 fills whole warps) and of 16 lines
 // (SEG even).  L is odd, which keeps the shared-memory rows conflict-free.  (96, 3) is the
-// parallel-cyclic-reduction end of the range: three rows per thread, seven PCR rounds.
+// parallel-cyclic-reduction end of the range: three rows per thread, seven PCR rounds.  (8, 13),
+// (10, 17), (12, 15) and (16, 15) cover lines of 97, 161 and 225 nodes with less than 10% padding.
 #define NPB_INNER_SEGS_X(X) X(4, 17) X(8, 9) X(8, 17) X(12, 11) X(12, 17) X(16, 9) X(16, 17) X(20, 13) X(24, 11) X(24, 17) X(32, 9) \
-    X(96, 3)
-#define NPB_INNER_SEGS_YZ(X) X(4, 17) X(8, 9) X(8, 17) X(10, 13) X(12, 17) X(16, 9) X(16, 17) X(20, 13) X(24, 11) X(24, 17) X(32, 9)
+    X(8, 13) X(12, 15) X(16, 15) X(96, 3)
+#define NPB_INNER_SEGS_YZ(X) X(4, 17) X(8, 9) X(8, 17) X(10, 13) X(12, 17) X(16, 9) X(16, 17) X(20, 13) X(24, 11) X(24, 17) X(32, 9) \
+    X(8, 13) X(10, 17) X(12, 15) X(16, 15)
 
 template <int DIR, int TX, int SEG, int L>
 static cudaError_t launch_inner_shape(const TmaLaunch &P, const TmaGeom &g, int flags, int sm_count, cudaStream_t st) {

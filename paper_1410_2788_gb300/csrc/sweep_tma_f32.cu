@@ -153,10 +153,10 @@ cudaError_t prepare_sweep_inner_x();
 cudaError_t prepare_sweep_inner_y();
 cudaError_t prepare_sweep_inner_z();
 
-static const int kInnerSegsX[][2] = {{4, 17}, {8, 9},   {8, 17},  {12, 11}, {12, 17}, {16, 9},
-                                     {16, 17}, {20, 13}, {24, 11}, {24, 17}, {32, 9}, {96, 3}};
-static const int kInnerSegsYZ[][2] = {{4, 17}, {8, 9},   {8, 17},  {10, 13}, {12, 17}, {16, 9},
-                                      {16, 17}, {20, 13}, {24, 11}, {24, 17}, {32, 9}};
+static const int kInnerSegsX[][2] = {{4, 17},  {8, 9},   {8, 17},  {12, 11}, {12, 17}, {16, 9},  {16, 17}, {20, 13},
+                                     {24, 11}, {24, 17}, {32, 9},  {8, 13},  {12, 15}, {16, 15}, {96, 3}};
+static const int kInnerSegsYZ[][2] = {{4, 17},  {8, 9},   {8, 17}, {10, 13}, {12, 17}, {16, 9},  {16, 17}, {20, 13},
+                                      {24, 11}, {24, 17}, {32, 9}, {8, 13},  {10, 17}, {12, 15}, {16, 15}};
 
 int inner_shapes(int dir, SweepShape *out, int max) {
     int n = 0;
@@ -172,8 +172,8 @@ int inner_shapes(int dir, SweepShape *out, int max) {
 SweepShape inner_default_shape(int dir, int n) {
     // rows solved (padding included) plus about eight rows' worth of work per segment for the
     // reduced system; the cheapest shape covering the n-2 unknowns
-    SweepShape t[32], best{0, 0, 0, 0};
-    const int k = inner_shapes(dir, t, 32);
+    SweepShape t[64], best{0, 0, 0, 0};
+    const int k = inner_shapes(dir, t, 64);
     auto cost = [](const SweepShape &s) { return s.seg * s.len + 8 * s.seg; };
     for (int i = 0; i < k; ++i) {
         if (t[i].seg * t[i].len < n - 2) continue;

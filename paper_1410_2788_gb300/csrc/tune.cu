@@ -87,14 +87,14 @@ extern "C" int npb_autotune(npb_grid *g, const npb_opts *o, int32_t reps, char *
 extern "C" int npb_tune_set(npb_ctx *ctx, int32_t precision, int32_t dir, int32_t n, int32_t kind, int32_t tx,
                             int32_t seg, int32_t len) {
     if (!ctx || dir < 0 || dir > 2 || kind < 0 || kind > 3) return fail(NPB_EINVAL, "bad argument");
-    SweepShape s{tx, seg, len, kind}, t[32];
+    SweepShape s{tx, seg, len, kind}, t[64];
     bool found = false;
     if (kind == 0) {
         found = sweep_shape_available(precision, s);
     } else if (precision == NPB_FP64) {
         found = kind == 3 && tx == 32 && seg == 2 && len == 1;  // Thomas per line, multipliers once per leg
     } else if (precision == NPB_FP32_SWEEP) {
-        const int k = kind == 1 ? tma_shapes(dir, t, 32) : (kind == 2 ? inner_shapes(dir, t, 32) : line_shapes(dir, t, 32));
+        const int k = kind == 1 ? tma_shapes(dir, t, 64) : (kind == 2 ? inner_shapes(dir, t, 64) : line_shapes(dir, t, 64));
         for (int i = 0; i < k && !found; ++i) found = t[i].tx == tx && t[i].seg == seg && t[i].len == len;
     }
     if (!found) return fail(NPB_EINVAL, "shape kind %d %d/%d/%d not instantiated", kind, tx, seg, len);

@@ -120,7 +120,7 @@ def test_stage_parity(npb, ctx, O, precision, tol, leg, scheme):
     _stage_check(npb, ctx, O, precision, tol, leg, scheme)
 
 
-@pytest.mark.parametrize("shape", range(24))
+@pytest.mark.parametrize("shape", range(30))
 @pytest.mark.parametrize("leg,scheme", [(0, 2), (2, 2), (1, 1), (3, 1), (0, 4), (1, 3)])
 def test_inner_sweep_stage_parity(npb, O, shape, leg, scheme):
     """The interior-row FP32 sweeps (kind 2) pinned for all three directions on the ragged
@@ -404,9 +404,9 @@ TMA_SHAPES = {0: [(8, 2, 17), (8, 4, 9), (8, 4, 17), (8, 8, 13), (8, 8, 17), (8,
               1: [(32, 2, 17), (32, 4, 9), (32, 4, 17), (32, 8, 13), (32, 8, 17), (32, 16, 11), (32, 16, 17),
                   (16, 4, 17), (16, 8, 13), (16, 8, 17), (16, 16, 11), (16, 16, 17), (16, 32, 9)]}
 _INNER_SEGS_8 = [(4, 17), (8, 9), (8, 17), (12, 11), (12, 17), (16, 9), (16, 17), (20, 13), (24, 11), (24, 17),
-                 (32, 9), (96, 3)]
+                 (32, 9), (8, 13), (12, 15), (16, 15), (96, 3)]
 _INNER_SEGS_16 = [(4, 17), (8, 9), (8, 17), (10, 13), (12, 17), (16, 9), (16, 17), (20, 13), (24, 11), (24, 17),
-                  (32, 9)]
+                  (32, 9), (8, 13), (10, 17), (12, 15), (16, 15)]
 INNER_SHAPES = {0: [(8, s, l) for s, l in _INNER_SEGS_8],
                 1: [(16, s, l) for s, l in _INNER_SEGS_16] + [(8, s, l) for s, l in _INNER_SEGS_8]}
 LINE_SHAPES = [(32, 2, 2), (32, 2, 1)]  # kind 3: 32 lines per tile, two threads per line, 2 or 1 stages
