@@ -416,9 +416,15 @@ __global__ void __launch_bounds__(TX *SEG, inner_min_blocks<TX * SEG>())
         al[L - 1] = E_;
         if (post_nl) {  // the outflowing nonlinear stage on the unknowns outside the molecule
             const uint32_t post = ~(nb >> 1) & (nrem >= 32 ? 0xffffffffu : (nrem > 0 ? (1u << nrem) - 1u : 0u));
+            if (nlq <= kNlSeriesMaxQ) {  // the leg's form chosen once, outside the row loop
 #pragma unroll
-            for (int k = 0; k < L; ++k)
-                if ((post >> k) & 1u) al[k] = nl_flow_leg(al[k], nlq, nlomq);
+                for (int k = 0; k < L; ++k)
+                    if ((post >> k) & 1u) al[k] = nl_flow_tanh(al[k], 2.0f * nlq);
+            } else {
+#pragma unroll
+                for (int k = 0; k < L; ++k)
+                    if ((post >> k) & 1u) al[k] = nl_flow(al[k], nlq, nlomq);
+            }
         }
         if (warp_full) {
 #pragma unroll

@@ -113,15 +113,16 @@ __device__ __forceinline__ float tanh_approx(float x) {
     return y;
 }
 
-// FP32 flow for small q from the hardware tanh: x = 2 q tanh(w/2) (|x| <= 2q <= 1/8) and
-// w' = 2 atanh(x/2) = x (1 + x^2/12 + x^4/80 + ...), truncated after x^4/80 (relative error below
-// x^6/448 < 1e-8).  tanh.approx.f32 carries a relative error near 2^-11, so |w'| is off by at most
-// 5e-4 of itself: at most 1e-6 kT/e on a leg with tau = 10 (q = 2.2e-4) and 1.5e-5 kT/e with tau = 5
-// (q = 0.015), far inside the FP32 path's tolerance.  One special-function operation and five others.
+// FP32 flow for small q from the hardware tanh: with t = tanh(w/2) and Q = 2q, x = Q t (|x| <= Q <=
+// 1/8) and w' = 2 atanh(x/2) = x (1 + x^2/12 + x^4/80 + ...) = t (Q + (Q^3/12) t^2), truncated after
+// x^2/12 (relative error below x^4/80 <= 3e-6).  tanh.approx.f32 carries a relative error near 2^-11,
+// so |w'| is off by at most 5e-4 of itself: at most 1e-6 kT/e on a leg with tau = 10 (q = 2.2e-4)
+// and 1.5e-5 kT/e with tau = 5 (q = 0.015), far inside the FP32 path's tolerance.  Q and Q^3/12 are
+// the leg's (hoisted out of the row loops): one special-function operation and four others.
 __device__ __forceinline__ float nl_flow_tanh(float w, float q2) {
-    const float x = q2 * tanh_approx(0.5f * w);
-    const float x2 = x * x;
-    return x * fmaf(x2, fmaf(x2, 1.0f / 80.0f, 1.0f / 12.0f), 1.0f);
+    const float t = tanh_approx(0.5f * w);
+    const float c3 = q2 * q2 * q2 * (1.0f / 12.0f);
+    return t * fmaf(c3, t * t, q2);
 }
 
 // The nonlinear stage with the leg's q.  FP64: the series where q is small (it replaces log1p and a
