@@ -565,6 +565,8 @@ LegDev npb::make_leg(const npb_grid *g, int leg, const npb_opts *o) {
     L.ent_x = g->d_ent_x;
     L.ent_qt = g->d_ent_qt;
     L.ent_xq = g->d_ent_xq;
+    L.ent_off = g->d_ent_off;
+    L.n_ent = g->sc.total;
     L.src = tau * 4.0 * kPi * kBjerrum / (h * h * h);
     L.eps_mode = o->eps_mode == NPB_EPS_MIDPOINT ? 1 : 0;
     for (int d = 0; d < 3; ++d) L.fac[d] = prec == NPB_FP64 ? g->d_fac[kLegSlot[leg]][d] : nullptr;
@@ -742,7 +744,8 @@ cudaError_t npb::launch_dir(npb_grid *g, int prec, int d, SweepShape shape, int 
 // (the one-tile-per-block kernels and the source stage read it).  FP32 legs use the
 // TMA-pipelined sweeps, in launches of up to kTmaMaxLegs legs, where every grid's geometry
 // allows it; otherwise the one-tile-per-block sweeps.  The source stage is fused into the x
-// sweep except with the kind-1 TMA kernel, which leaves it to its own sparse launch.
+// sweep, except with the kind-1 TMA kernel and for large charge lists, where it is a launch of
+// its own over the charge entries.
 int npb::step_legs(npb_ctx *ctx, const LegRef *refs, int n, const LegDev *d_table, int prec, int scheme,
                    cudaStream_t st) {
     if (n <= 0) return 0;
@@ -781,12 +784,15 @@ int npb::step_legs(npb_ctx *ctx, const LegRef *refs, int n, const LegDev *d_tabl
     // (after a fused S); elsewhere it is its own launch before each sweep
     bool cn_fused = cn;
     for (int d = 0; d < 3; ++d) cn_fused = cn_fused && tma[d] && shape[d].kind == 2;
-    // LODIE2's source stage: fused into the x sweep's load except by the kind-1 TMA kernel and before
-    // an explicit half step of its own launch
-    const bool src_apart = !first_n && ((cn && !cn_fused) || (tma[0] && shape[0].kind == 1));
+    // LODIE2's source stage: fused into the x sweep's load except by the kind-1 TMA kernel, before
+    // an explicit half step of its own launch, and for charge lists of kSourceApartEntries or more
+    int ent_max = 1;  // bound on the legs' charge entries (8 trilinear nodes per atom)
+    for (int i = 0; i < n; ++i) ent_max = std::max(ent_max, 8 * refs[i].g->n_atoms);
+    const bool src_apart =
+        !first_n && ((cn && !cn_fused) || (tma[0] && (shape[0].kind == 1 || ent_max >= kSourceApartEntries)));
     if (src_apart) {
         if ((rc = pr.begin(st, &ev))) return rc;
-        CU(launch_source(prec, d_table, n, ny, nz, st));
+        CU(launch_source_entries(prec, d_table, n, ent_max, st));
         if ((rc = pr.end(st, ev, K_SOURCE))) return rc;
     }
     if (cn && first_n && !cn_fused) {

@@ -53,6 +53,8 @@ struct LegDev {
     int32_t eps_mode;          // 0 harmonic, 1 midpoint
     float rEf[3], nl_qf, nl_omqf, srcf;  // the same constants rounded once to FP32 (FP32 sweeps)
     const int2 *ent_xq;                  // charge entries as (x | y << 16, FP32 qtilde), ent_x's order
+    const int64_t *ent_off;              // element offset of each entry's node in the state
+    const int32_t *n_ent;                // number of entries (device)
     // FP32 legs, per direction: the Thomas multipliers (m_j, cp_j) of a line whose half points all
     // carry the leg's r*eps outside the molecule (r*eps_in for vacuum legs), j = 1 .. ceil((n-2)/2);
     // the line-per-thread-pair sweeps use them on tiles of constant coefficients (null: no table)
@@ -108,6 +110,13 @@ int sweep_shapes(int prec, SweepShape *out, int max);
 
 cudaError_t launch_nonlinear(int prec, const LegDev *legs_dev, int n_legs, int nx, int ny, int nz,
                              cudaStream_t st);
+// Charge lists of at least this many entries (bound: 8 per atom) take LODIE2's S as a launch of its
+// own before the x sweep; the fused form costs the x sweep's tiles with charges a block barrier
+// and a dependent load chain each, which outweighs the extra launch on large molecules only.
+constexpr int kSourceApartEntries = 65536;
+// LODIE2's S over the charge entries, one thread per entry for all n_legs legs; n_ent_max bounds
+// every leg's entry count.
+cudaError_t launch_source_entries(int prec, const LegDev *legs_dev, int n_legs, int n_ent_max, cudaStream_t st);
 cudaError_t launch_source(int prec, const LegDev *legs_dev, int n_legs, int ny, int nz,
                           cudaStream_t st);
 struct GridGeom;

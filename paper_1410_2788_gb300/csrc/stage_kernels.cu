@@ -10,6 +10,7 @@
 //               tree; the last block to finish sums the block partials in a fixed tree), so the
 //               value does not depend on scheduling.
 #include <algorithm>
+#include <type_traits>
 
 #include "npb_internal.cuh"
 #include "setup_kernels.cuh"
@@ -234,6 +235,32 @@ cudaError_t launch_additive_combine(int prec, const AddLeg *legs, int n_legs, in
     dim3 grid(152 * 4, 1, n_legs);
     if (prec == 0) k_additive_combine<double><<<grid, 256, 0, st>>>(legs, aos);
     else k_additive_combine<float><<<grid, 256, 0, st>>>(legs, aos);
+    return cudaGetLastError();
+}
+
+// S at the charge entries: thread e adds tau Q at entry e of every leg (the entries are distinct
+// nodes, so the adds do not collide; legs of one grid share the entry arrays, and their adds are
+// independent, so they overlap).  FP32 legs add srcf * qtilde in FP32, as the x sweeps' fused
+// source does.
+template <typename T>
+__global__ void k_source_entries(const LegDev *__restrict__ legs, int n_legs) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+#pragma unroll 4
+    for (int j = 0; j < n_legs; ++j) {
+        const LegDev &lg = legs[j];
+        if (e >= *lg.n_ent) continue;
+        T *u = static_cast<T *>(lg.u);
+        const int64_t p = lg.ent_off[e];
+        if constexpr (std::is_same<T, float>::value) u[p] = fmaf(lg.srcf, __int_as_float(lg.ent_xq[e].y), u[p]);
+        else u[p] += lg.src * lg.ent_qt[e];
+    }
+}
+
+cudaError_t launch_source_entries(int prec, const LegDev *legs, int n_legs, int n_ent_max, cudaStream_t st) {
+    if (n_legs < 1 || n_ent_max < 1) return cudaSuccess;
+    const unsigned blocks = (unsigned)((n_ent_max + 255) / 256);
+    if (prec == 0) k_source_entries<double><<<blocks, 256, 0, st>>>(legs, n_legs);
+    else k_source_entries<float><<<blocks, 256, 0, st>>>(legs, n_legs);
     return cudaGetLastError();
 }
 

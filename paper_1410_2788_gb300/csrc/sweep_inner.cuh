@@ -226,7 +226,8 @@ __global__ void __launch_bounds__(TX *SEG, inner_min_blocks<TX * SEG>())
     auto src_apply = [&](int q, int2 v) {  // one entry into stage q's rows
         const int4 ti = tinfo[q];
         const int l = (v.x >> 16) - (1 + ti.y * TX), x = v.x & 0xffff;
-        data(q)[l * P.sx + x] += legp(ti.x).srcf * __int_as_float(v.y);
+        float &d = data(q)[l * P.sx + x];
+        d = fmaf(legp(ti.x).srcf, __int_as_float(v.y), d);
     };
     if (fuse_src && t < total) {
         int tb, te;
