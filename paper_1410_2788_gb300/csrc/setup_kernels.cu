@@ -277,40 +277,109 @@ __device__ __forceinline__ void face_node(int64_t f, int nx, int ny, int nz, int
 
 constexpr int kAtomChunk = 256;
 
-// Both media's faces in one pass, FP32 pair terms (chunk sums in FP32, chunks accumulated in
-// FP64): solvent C sum q exp(-kbar d / sqrt(eps_out)) / (eps_out d), vacuum C sum q / (eps_in d).
-// The two share the distance and its reciprocal square root; each thread holds kFaceBlock face
-// nodes, so every atom read from shared memory serves several nodes.
-constexpr int kFaceBlock = 4;
-
 __device__ __forceinline__ float ex2_approx(float x) {
     float r;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
 
-__global__ void k_boundary_pair_f32(GridGeom g, const double *__restrict__ xyz, const double *__restrict__ q,
-                                    int n_atoms, double eps_s, double kbar, double eps_v,
+// Face rows: each thread takes kRowBlock adjacent nodes of one face row, all six faces in one
+// launch.  A block serves one face type (ft 0: the z faces, rows along x at fixed y; 1: the y
+// faces, rows along x at fixed z; 2: the x faces, rows along y at fixed z), blocks [0, b0) type 0,
+// [b0, b0 + b1) type 1, the rest type 2.  Per atom the two fixed-coordinate differences and the
+// sum of their squares serve the row's nodes, so a pair term costs one subtraction and one fused
+// multiply-add for its squared distance instead of six operations.
+constexpr int kRowBlock = 4;
+
+struct FaceRow {
+    int ft;          // face type
+    int64_t f0;      // compact face index of the first node; the next nodes follow at +1
+    int n_here;      // nodes of the row this thread owns (0: none)
+    int i0, j0, k0;  // grid indices of the first node
+};
+
+__device__ __forceinline__ FaceRow face_row(int nx, int ny, int nz, int b0, int b1) {
+    FaceRow R{};
+    const int64_t A = (int64_t)nx * ny, B = (int64_t)nx * (nz - 2), Cc = (int64_t)(ny - 2) * (nz - 2);
+    R.ft = (int)blockIdx.x < b0 ? 0 : ((int)blockIdx.x < b0 + b1 ? 1 : 2);
+    const int blk = (int)blockIdx.x - (R.ft == 0 ? 0 : (R.ft == 1 ? b0 : b0 + b1));
+    const int len = R.ft == 2 ? ny - 2 : nx;  // nodes per row
+    const int rows = R.ft == 0 ? ny : nz - 2;  // rows per face
+    const int chunks = (len + kRowBlock - 1) / kRowBlock;
+    const int64_t items = 2LL * rows * chunks;
+    const int64_t it = (int64_t)blk * blockDim.x + threadIdx.x;
+    const bool live = it < items;
+    const int side = live ? (int)(it / ((int64_t)rows * chunks)) : 0;
+    const int64_t rr = live ? it % ((int64_t)rows * chunks) : 0;
+    const int row = (int)(rr / chunks), ch = (int)(rr % chunks);
+    if (R.ft == 0) {
+        R.k0 = side ? nz - 1 : 0;
+        R.j0 = row;
+        R.i0 = ch * kRowBlock;
+        R.f0 = (side ? A : 0) + (int64_t)R.j0 * nx + R.i0;
+    } else if (R.ft == 1) {
+        R.j0 = side ? ny - 1 : 0;
+        R.k0 = 1 + row;
+        R.i0 = ch * kRowBlock;
+        R.f0 = 2 * A + (side ? B : 0) + (int64_t)row * nx + R.i0;
+    } else {
+        R.i0 = side ? nx - 1 : 0;
+        R.k0 = 1 + row;
+        R.j0 = 1 + ch * kRowBlock;
+        R.f0 = 2 * A + 2 * B + (side ? Cc : 0) + (int64_t)row * (ny - 2) + (R.j0 - 1);
+    }
+    R.n_here = live ? min(kRowBlock, len - ch * kRowBlock) : 0;
+    return R;
+}
+
+// Blocks of each face type for the row kernels (t threads per block).
+static void face_row_blocks(const GridGeom &g, int t, int &b0, int &b1, int &b2) {
+    const int64_t cz = (g.nx + kRowBlock - 1) / kRowBlock, cx = (g.ny - 2 + kRowBlock - 1) / kRowBlock;
+    const int64_t n0 = 2LL * g.ny * cz, n1 = 2LL * (g.nz - 2) * cz, n2 = 2LL * (g.nz - 2) * cx;
+    b0 = (int)((n0 + t - 1) / t);
+    b1 = (int)((n1 + t - 1) / t);
+    b2 = (int)((n2 + t - 1) / t);
+}
+
+// FP32 pair terms of one atom chunk for a row along x (ALONG_Y false) or y.
+template <bool ALONG_Y>
+__device__ __forceinline__ void face_row_sums(const float4 *sa, int na, const float *w, float fu, float fv, float c,
+                                              bool coulomb, float *ps, float *pv) {
+    for (int t = 0; t < na; ++t) {
+        const float4 P = sa[t];
+        const float pw = ALONG_Y ? P.y : P.x, pu = ALONG_Y ? P.x : P.y;
+        const float du = fu - pu, dv = fv - P.z;
+        const float uv2 = fmaf(du, du, dv * dv);
+#pragma unroll
+        for (int r = 0; r < kRowBlock; ++r) {
+            const float dw = w[r] - pw;
+            const float d2 = fmaf(dw, dw, uv2);
+            const float id = rsqrtf(d2);
+            const float qi = P.w * id;
+            pv[r] += qi;
+            if (!coulomb) ps[r] = fmaf(qi, ex2_approx(c * (d2 * id)), ps[r]);
+        }
+    }
+}
+
+// Both media's faces, FP32 pair terms (chunk sums in FP32, chunks accumulated in FP64):
+// solvent C sum q exp(-kbar d / sqrt(eps_out)) / (eps_out d), vacuum C sum q / (eps_in d).
+__global__ void k_boundary_rows_f32(GridGeom g, const double *__restrict__ xyz, const double *__restrict__ q,
+                                    int n_atoms, double eps_s, double kbar, double eps_v, int b0, int b1,
                                     double *__restrict__ out_s, double *__restrict__ out_v) {
     __shared__ float4 sa[kAtomChunk];
-    const int64_t nf = face_count(g.nx, g.ny, g.nz);
-    const int64_t f0 = (int64_t)blockIdx.x * blockDim.x * kFaceBlock + threadIdx.x;
-    float x[kFaceBlock], y[kFaceBlock], z[kFaceBlock];
+    const FaceRow R = face_row(g.nx, g.ny, g.nz, b0, b1);
+    // positions relative to the grid origin keep FP32 resolution near 1e-5 A
+    float w[kRowBlock];  // the row's coordinate of each node
 #pragma unroll
-    for (int r = 0; r < kFaceBlock; ++r) {
-        int i = 0, j = 0, k = 0;
-        const int64_t f = f0 + (int64_t)r * blockDim.x;
-        if (f < nf) face_node(f, g.nx, g.ny, g.nz, i, j, k);
-        // positions relative to the grid origin keep FP32 resolution near 1e-5 A
-        x[r] = (float)(i * g.h);
-        y[r] = (float)(j * g.h);
-        z[r] = (float)(k * g.h);
-    }
+    for (int r = 0; r < kRowBlock; ++r) w[r] = R.ft == 2 ? (float)((R.j0 + r) * g.h) : (float)((R.i0 + r) * g.h);
+    const float fu = R.ft == 2 ? (float)(R.i0 * g.h) : (float)(R.j0 * g.h);  // fixed: x (type 2) or y
+    const float fv = (float)(R.k0 * g.h);                                     // fixed: z
     const float c = (float)(-kbar / sqrt(eps_s) * 1.4426950408889634);  // -kbar/sqrt(eps) * log2(e)
     const bool coulomb = kbar == 0.0;
-    double ss[kFaceBlock], sv[kFaceBlock];
+    double ss[kRowBlock], sv[kRowBlock];
 #pragma unroll
-    for (int r = 0; r < kFaceBlock; ++r) ss[r] = sv[r] = 0.0;
+    for (int r = 0; r < kRowBlock; ++r) ss[r] = sv[r] = 0.0;
     for (int a0 = 0; a0 < n_atoms; a0 += kAtomChunk) {
         __syncthreads();
         for (int t = threadIdx.x; t < kAtomChunk && a0 + t < n_atoms; t += blockDim.x)
@@ -318,100 +387,78 @@ __global__ void k_boundary_pair_f32(GridGeom g, const double *__restrict__ xyz, 
                                 (float)(xyz[3 * (a0 + t) + 2] - g.oz), (float)q[a0 + t]);
         __syncthreads();
         const int na = min(kAtomChunk, n_atoms - a0);
-        float ps[kFaceBlock], pv[kFaceBlock];
+        float ps[kRowBlock], pv[kRowBlock];
 #pragma unroll
-        for (int r = 0; r < kFaceBlock; ++r) ps[r] = pv[r] = 0.f;
-        if (coulomb) {
-            for (int t = 0; t < na; ++t) {
-                const float4 A = sa[t];
+        for (int r = 0; r < kRowBlock; ++r) ps[r] = pv[r] = 0.f;
+        if (R.ft == 2) face_row_sums<true>(sa, na, w, fu, fv, c, coulomb, ps, pv);
+        else face_row_sums<false>(sa, na, w, fu, fv, c, coulomb, ps, pv);
 #pragma unroll
-                for (int r = 0; r < kFaceBlock; ++r) {
-                    const float dx = x[r] - A.x, dy = y[r] - A.y, dz = z[r] - A.z;
-                    pv[r] = fmaf(A.w, rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))), pv[r]);
-                }
-            }
-#pragma unroll
-            for (int r = 0; r < kFaceBlock; ++r) ps[r] = pv[r];
-        } else {
-            for (int t = 0; t < na; ++t) {
-                const float4 A = sa[t];
-#pragma unroll
-                for (int r = 0; r < kFaceBlock; ++r) {
-                    const float dx = x[r] - A.x, dy = y[r] - A.y, dz = z[r] - A.z;
-                    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    const float id = rsqrtf(d2);
-                    const float qi = A.w * id;
-                    pv[r] += qi;
-                    ps[r] = fmaf(qi, ex2_approx(c * (d2 * id)), ps[r]);
-                }
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < kFaceBlock; ++r) {
-            ss[r] += (double)ps[r];
+        for (int r = 0; r < kRowBlock; ++r) {
+            ss[r] += (double)(coulomb ? pv[r] : ps[r]);
             sv[r] += (double)pv[r];
         }
     }
 #pragma unroll
-    for (int r = 0; r < kFaceBlock; ++r) {
-        const int64_t f = f0 + (int64_t)r * blockDim.x;
-        if (f < nf) {
-            out_s[f] = kBjerrum / eps_s * ss[r];
-            out_v[f] = kBjerrum / eps_v * sv[r];
+    for (int r = 0; r < kRowBlock; ++r)
+        if (r < R.n_here) {
+            out_s[R.f0 + r] = kBjerrum / eps_s * ss[r];
+            out_v[R.f0 + r] = kBjerrum / eps_v * sv[r];
+        }
+}
+
+// FP64 pair terms of one atom chunk for a row along x (ALONG_Y false) or y, atoms in index order.
+template <bool ALONG_Y>
+__device__ __forceinline__ void face_row_sums64(const double4_32a *sa, int na, const double *w, double fu, double fv,
+                                                double ks, double *ss, double *sv) {
+    for (int t = 0; t < na; ++t) {
+        const double4_32a P = sa[t];
+        const double pw = ALONG_Y ? P.y : P.x, pu = ALONG_Y ? P.x : P.y;
+        const double du = fu - pu, dv = fv - P.z;
+        const double uv2 = du * du + dv * dv;
+#pragma unroll
+        for (int r = 0; r < kRowBlock; ++r) {
+            const double dw = w[r] - pw;
+            const double d2 = dw * dw + uv2;
+            const double id = rsqrt(d2);
+            const double qi = P.w * id;
+            sv[r] += qi;
+            ss[r] += ks == 0.0 ? qi : qi * exp(-ks * (d2 * id));
         }
     }
 }
 
-// Both media's faces in one pass, FP64 pair terms (the parity path): the two sums share the
-// distance, taken as d^2 * rsqrt(d^2), and 1/d = rsqrt(d^2); only the solvent's screening needs its
-// exponential.  Each thread holds kFaceBlock face nodes; the atoms are summed in index order.
-__global__ void k_boundary_pair_f64(GridGeom g, const double *__restrict__ xyz, const double *__restrict__ q,
-                                    int n_atoms, double eps_s, double kbar, double eps_v,
+// Both media's faces, FP64 pair terms (the parity path): the two sums share the distance, taken
+// as d^2 * rsqrt(d^2), and 1/d = rsqrt(d^2); only the solvent's screening needs its exponential.
+__global__ void k_boundary_rows_f64(GridGeom g, const double *__restrict__ xyz, const double *__restrict__ q,
+                                    int n_atoms, double eps_s, double kbar, double eps_v, int b0, int b1,
                                     double *__restrict__ out_s, double *__restrict__ out_v) {
-    __shared__ double4 sa[kAtomChunk];
-    const int64_t nf = face_count(g.nx, g.ny, g.nz);
-    const int64_t f0 = (int64_t)blockIdx.x * blockDim.x * kFaceBlock + threadIdx.x;
-    double x[kFaceBlock], y[kFaceBlock], z[kFaceBlock];
+    __shared__ double4_32a sa[kAtomChunk];
+    const FaceRow R = face_row(g.nx, g.ny, g.nz, b0, b1);
+    double w[kRowBlock];
 #pragma unroll
-    for (int r = 0; r < kFaceBlock; ++r) {
-        int i = 0, j = 0, k = 0;
-        const int64_t f = f0 + (int64_t)r * blockDim.x;
-        if (f < nf) face_node(f, g.nx, g.ny, g.nz, i, j, k);
-        x[r] = node_coord(g.ox, i, g.h);
-        y[r] = node_coord(g.oy, j, g.h);
-        z[r] = node_coord(g.oz, k, g.h);
-    }
+    for (int r = 0; r < kRowBlock; ++r)
+        w[r] = R.ft == 2 ? node_coord(g.oy, R.j0 + r, g.h) : node_coord(g.ox, R.i0 + r, g.h);
+    const double fu = R.ft == 2 ? node_coord(g.ox, R.i0, g.h) : node_coord(g.oy, R.j0, g.h);
+    const double fv = node_coord(g.oz, R.k0, g.h);
     const double ks = kbar / sqrt(eps_s);
-    double ss[kFaceBlock], sv[kFaceBlock];
+    double ss[kRowBlock], sv[kRowBlock];
 #pragma unroll
-    for (int r = 0; r < kFaceBlock; ++r) ss[r] = sv[r] = 0.0;
+    for (int r = 0; r < kRowBlock; ++r) ss[r] = sv[r] = 0.0;
     for (int a0 = 0; a0 < n_atoms; a0 += kAtomChunk) {
         __syncthreads();
         for (int t = threadIdx.x; t < kAtomChunk && a0 + t < n_atoms; t += blockDim.x)
-            sa[t] = make_double4(xyz[3 * (a0 + t)], xyz[3 * (a0 + t) + 1], xyz[3 * (a0 + t) + 2], q[a0 + t]);
+            sa[t] = make_double4_32a(xyz[3 * (a0 + t)], xyz[3 * (a0 + t) + 1], xyz[3 * (a0 + t) + 2], q[a0 + t]);
         __syncthreads();
         const int na = min(kAtomChunk, n_atoms - a0);
-        for (int t = 0; t < na; ++t) {
-            const double4 A = sa[t];
-#pragma unroll
-            for (int r = 0; r < kFaceBlock; ++r) {
-                const double dx = x[r] - A.x, dy = y[r] - A.y, dz = z[r] - A.z;
-                const double d2 = dx * dx + dy * dy + dz * dz;
-                const double id = rsqrt(d2);
-                const double qi = A.w * id;
-                sv[r] += qi;
-                ss[r] += ks == 0.0 ? qi : qi * exp(-ks * (d2 * id));
-            }
-        }
+        if (R.ft == 2) face_row_sums64<true>(sa, na, w, fu, fv, ks, ss, sv);
+        else face_row_sums64<false>(sa, na, w, fu, fv, ks, ss, sv);
     }
 #pragma unroll
-    for (int r = 0; r < kFaceBlock; ++r) {
-        const int64_t f = f0 + (int64_t)r * blockDim.x;
-        if (f < nf) {
-            out_s[f] = kBjerrum / eps_s * ss[r];
-            out_v[f] = kBjerrum / eps_v * sv[r];
+    for (int r = 0; r < kRowBlock; ++r)
+        if (r < R.n_here) {
+            out_s[R.f0 + r] = kBjerrum / eps_s * ss[r];
+            out_v[R.f0 + r] = kBjerrum / eps_v * sv[r];
         }
-    }
 }
 
 // Zero interior, Dirichlet faces, zero padding: the initial state of a leg (Sec. 2.2).
@@ -538,14 +585,16 @@ cudaError_t setup_charges(const GridGeom &g, const double *xyz, const double *q,
 cudaError_t setup_boundary_pair(const GridGeom &g, const double *xyz, const double *q, int n_atoms, double eps_out,
                                 double kbar, double eps_in, double *out_s, double *out_v, cudaStream_t st,
                                 bool fp64) {
-    const int64_t nf = face_count(g.nx, g.ny, g.nz);
+    // one launch over the rows of all six faces, kRowBlock adjacent nodes per thread
     const int t = 128;
+    int b0, b1, b2;
+    face_row_blocks(g, t, b0, b1, b2);
     if (fp64)
-        k_boundary_pair_f64<<<blocks_for(nf, (int64_t)t * kFaceBlock), t, 0, st>>>(g, xyz, q, n_atoms, eps_out, kbar,
-                                                                                   eps_in, out_s, out_v);
+        k_boundary_rows_f64<<<b0 + b1 + b2, t, 0, st>>>(g, xyz, q, n_atoms, eps_out, kbar, eps_in, b0, b1, out_s,
+                                                         out_v);
     else
-        k_boundary_pair_f32<<<blocks_for(nf, (int64_t)t * kFaceBlock), t, 0, st>>>(g, xyz, q, n_atoms, eps_out, kbar,
-                                                                                   eps_in, out_s, out_v);
+        k_boundary_rows_f32<<<b0 + b1 + b2, t, 0, st>>>(g, xyz, q, n_atoms, eps_out, kbar, eps_in, b0, b1, out_s,
+                                                         out_v);
     return cudaGetLastError();
 }
 

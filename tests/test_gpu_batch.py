@@ -164,3 +164,25 @@ def test_shape_pinned_after_a_captured_solve_takes_effect(npb):
             npb.npb_grid_destroy(g)
     finally:
         npb.npb_ctx_destroy(c)
+
+
+def test_source_launch_of_its_own_equals_fused(npb, O):
+    """Large charge lists (8,300 atoms: 66,400 entry slots) take LODIE2's S as a launch of its own
+    over the charge entries before the x sweep; the batched path keeps it fused into the x sweep's
+    load.  Both add the same FP32 product to the same node value, so the energies agree bit for
+    bit, and with the oracle to 1e-4."""
+    p = I.random_walk_molecule(8300, 177, 0.5, seed=I.SEED_BASE + 310)
+    assert 8 * p.n_atoms >= 65536
+    o = npb.make_opts(0.4, 0.04, 6, precision=1)
+    c = npb.npb_ctx_create(0, 0)
+    try:
+        g = npb.npb_grid_create(c, p)
+        try:
+            single = npb.npb_energy(g, o)
+            assert npb.npb_energy_batch([g], o) == [single]
+        finally:
+            npb.npb_grid_destroy(g)
+    finally:
+        npb.npb_ctx_destroy(c)
+    ref = O.energy(p, 10.0, 6)
+    assert abs(single - ref) <= 1e-4 * abs(ref), (single, ref)
