@@ -288,8 +288,10 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // faces, rows along x at fixed z; 2: the x faces, rows along y at fixed z), blocks [0, b0) type 0,
 // [b0, b0 + b1) type 1, the rest type 2.  Per atom the two fixed-coordinate differences and the
 // sum of their squares serve the row's nodes, so a pair term costs one subtraction and one fused
-// multiply-add for its squared distance instead of six operations.
-constexpr int kRowBlock = 4;
+// multiply-add for its squared distance instead of six operations.  Two nodes per thread keep
+// about 40 warps on each SM at 257^3, enough to feed the special-function unit (rsqrt and exp2
+// per pair term), which bounds the kernel; four nodes (20 warps) ran 9% slower.
+constexpr int kRowBlock = 2;
 
 struct FaceRow {
     int ft;          // face type
