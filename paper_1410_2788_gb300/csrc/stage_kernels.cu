@@ -239,20 +239,36 @@ cudaError_t launch_additive_combine(int prec, const AddLeg *legs, int n_legs, in
 }
 
 // S at the charge entries: thread e adds tau Q at entry e of every leg (the entries are distinct
-// nodes, so the adds do not collide; legs of one grid share the entry arrays, and their adds are
-// independent, so they overlap).  FP32 legs add srcf * qtilde in FP32, as the x sweeps' fused
-// source does.
+// nodes, so the adds do not collide).  Legs go in groups of four, every load of a group issued
+// before its stores, so that the four read-modify-writes overlap (the compiler cannot move a load
+// of one leg's state above a store to another's).  FP32 legs add srcf * qtilde in FP32, as the x
+// sweeps' fused source does.
 template <typename T>
 __global__ void k_source_entries(const LegDev *__restrict__ legs, int n_legs) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
-#pragma unroll 4
-    for (int j = 0; j < n_legs; ++j) {
-        const LegDev &lg = legs[j];
-        if (e >= *lg.n_ent) continue;
-        T *u = static_cast<T *>(lg.u);
-        const int64_t p = lg.ent_off[e];
-        if constexpr (std::is_same<T, float>::value) u[p] = fmaf(lg.srcf, __int_as_float(lg.ent_xq[e].y), u[p]);
-        else u[p] += lg.src * lg.ent_qt[e];
+    for (int j0 = 0; j0 < n_legs; j0 += 4) {
+        T *u[4], v[4], a[4];
+        int64_t p[4];
+        bool ok[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int j = j0 + k;
+            ok[k] = j < n_legs && e < *legs[j].n_ent;
+            if (ok[k]) {
+                const LegDev &lg = legs[j];
+                u[k] = static_cast<T *>(lg.u);
+                p[k] = lg.ent_off[e];
+                if constexpr (std::is_same<T, float>::value) a[k] = __int_as_float(lg.ent_xq[e].y);
+                else a[k] = lg.src * lg.ent_qt[e];
+                v[k] = u[k][p[k]];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (ok[k]) {
+                if constexpr (std::is_same<T, float>::value) u[k][p[k]] = fmaf(legs[j0 + k].srcf, a[k], v[k]);
+                else u[k][p[k]] = v[k] + a[k];
+            }
     }
 }
 
