@@ -336,8 +336,9 @@ int npb_tune_load(npb_ctx *ctx, const char *path, int32_t *n_loaded);
  * stage of the method): direction dir (0 = x, 1 = y, 2 = z) over the legs of slots [0, n_legs)
  * -- n_legs = 4 is the launch of LOD steps 1 .. n (all four legs of Eq. deltaG3's RE+V solve),
  * n_legs = 2 the launch of steps n+1 .. 2n (the dt/2 legs) -- with the solve's shape for that
- * direction and its fused stages (LODIE2: S in the x sweep, N in the z sweep; LODIE1: N in the x
- * sweep).  reps launches are captured in one CUDA graph on the context stream (which must not be
+ * direction and its fused stages (LODIE2: S in the x sweep, N in the z sweep, except that S is a
+ * launch of its own, left out of the timing, where a solve gives it one: FP32 grids of 8,192 atoms
+ * or more, and the kind-1 sweeps; LODIE1: N in the x sweep).  reps launches are captured in one CUDA graph on the context stream (which must not be
  * the legacy default stream), replayed once untimed, then `rounds` times between two CUDA events;
  * *ms_per_launch = elapsed / (reps * rounds).  The legs' states are overwritten.  Implicit-Euler
  * LOD schemes only (NPB_EINVAL otherwise). */

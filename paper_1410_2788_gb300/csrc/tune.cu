@@ -137,10 +137,14 @@ extern "C" int npb_sweep_time(npb_grid *g, const npb_opts *o, int32_t dir, int32
     const int legs[4] = {0, 1, 2, 3};
     if ((rc = init_legs(g, o->precision, legs, 4, st))) return rc;
     const int n_dir[3] = {g->geo.nx, g->geo.ny, g->geo.nz};
-    int flags = 0;
-    if (o->scheme == NPB_LODIE2) flags = dir == 0 ? FUSE_PRE_SRC : (dir == 2 ? FUSE_POST_NL : 0);
-    else if (dir == 0) flags = FUSE_PRE_NL;
     const SweepShape s = shape_for(ctx, o->precision, dir, n_dir[dir]);
+    // the stages fused as a solve fuses them: S leaves the x sweep where the solve gives it a
+    // launch of its own (kind-1 TMA sweeps, large charge lists)
+    const bool src_apart = o->precision == NPB_FP32_SWEEP && s.kind >= 1 && g->tma_ok[0] &&
+                           (s.kind == 1 || 8 * g->n_atoms >= kSourceApartEntries);
+    int flags = 0;
+    if (o->scheme == NPB_LODIE2) flags = dir == 0 ? (src_apart ? 0 : FUSE_PRE_SRC) : (dir == 2 ? FUSE_POST_NL : 0);
+    else if (dir == 0) flags = FUSE_PRE_NL;
     cudaGraph_t graph;
     CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
