@@ -791,8 +791,28 @@ int npb::step_legs(npb_ctx *ctx, const LegRef *refs, int n, const LegDev *d_tabl
     const bool src_apart =
         !first_n && ((cn && !cn_fused) || (tma[0] && (shape[0].kind == 1 || ent_max >= kSourceApartEntries)));
     if (src_apart) {
+        bool one_grid = n <= 4;  // legs of one grid: everything by value, no table reads
+        for (int i = 1; i < n && one_grid; ++i) one_grid = refs[i].g == refs[0].g;
         if ((rc = pr.begin(st, &ev))) return rc;
-        CU(launch_source_entries(prec, d_table, n, ent_max, st));
+        if (one_grid) {
+            SourceLegs S{};
+            const npb_grid *g0 = refs[0].g;
+            for (int i = 0; i < n; ++i) {
+                const LegDev &L = g0->h_legs[prec][refs[i].slot];
+                S.u[i] = L.u;
+                S.srcf[i] = L.srcf;
+                S.src[i] = L.src;
+            }
+            S.ent_off = g0->d_ent_off;
+            S.ent_xq = g0->d_ent_xq;
+            S.ent_qt = g0->d_ent_qt;
+            S.n_ent = g0->sc.total;
+            S.n_slots = 8 * g0->n_atoms;
+            S.n_legs = n;
+            CU(launch_source_legs(prec, S, st));
+        } else {
+            CU(launch_source_entries(prec, d_table, n, ent_max, st));
+        }
         if ((rc = pr.end(st, ev, K_SOURCE))) return rc;
     }
     if (cn && first_n && !cn_fused) {

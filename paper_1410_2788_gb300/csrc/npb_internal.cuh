@@ -114,6 +114,21 @@ cudaError_t launch_nonlinear(int prec, const LegDev *legs_dev, int n_legs, int n
 // own before the x sweep; the fused form costs the x sweep's tiles with charges a block barrier
 // and a dependent load chain each, which outweighs the extra launch on large molecules only.
 constexpr int kSourceApartEntries = 65536;
+// LODIE2's S for up to four legs of one grid, everything a thread needs passed by value (no leg
+// table to read first): the legs' states and source factors, the grid's charge entries and the
+// device count of them.
+struct SourceLegs {
+    void *u[4];
+    float srcf[4];
+    double src[4];
+    const int64_t *ent_off;
+    const int2 *ent_xq;
+    const double *ent_qt;
+    const int32_t *n_ent;
+    int n_slots;  // allocated entry slots (8 per atom), a bound on *n_ent
+    int n_legs;
+};
+cudaError_t launch_source_legs(int prec, const SourceLegs &S, cudaStream_t st);
 // LODIE2's S over the charge entries, one thread per entry for all n_legs legs; n_ent_max bounds
 // every leg's entry count.
 cudaError_t launch_source_entries(int prec, const LegDev *legs_dev, int n_legs, int n_ent_max, cudaStream_t st);

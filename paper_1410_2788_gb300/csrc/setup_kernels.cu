@@ -343,10 +343,20 @@ static void face_row_blocks(const GridGeom &g, int t, int &b0, int &b1, int &b2)
     b2 = (int)((n2 + t - 1) / t);
 }
 
-// FP32 pair terms of one atom chunk for a row along x (ALONG_Y false) or y.
-template <bool ALONG_Y>
+// The hardware reciprocal square root, flushing subnormals (d^2 at a face node is at least the
+// squared distance from the face to the molecule, far above them).
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// FP32 pair terms of one atom chunk for a row along x (ALONG_Y false) or y; COULOMB: no screening
+// (kbar = 0), the solvent sum is the vacuum one.
+template <bool ALONG_Y, bool COULOMB>
 __device__ __forceinline__ void face_row_sums(const float4 *sa, int na, const float *w, float fu, float fv, float c,
-                                              bool coulomb, float *ps, float *pv) {
+                                              float *ps, float *pv) {
+#pragma unroll 4
     for (int t = 0; t < na; ++t) {
         const float4 P = sa[t];
         const float pw = ALONG_Y ? P.y : P.x, pu = ALONG_Y ? P.x : P.y;
@@ -356,10 +366,10 @@ __device__ __forceinline__ void face_row_sums(const float4 *sa, int na, const fl
         for (int r = 0; r < kRowBlock; ++r) {
             const float dw = w[r] - pw;
             const float d2 = fmaf(dw, dw, uv2);
-            const float id = rsqrtf(d2);
+            const float id = rsqrt_approx(d2);
             const float qi = P.w * id;
             pv[r] += qi;
-            if (!coulomb) ps[r] = fmaf(qi, ex2_approx(c * (d2 * id)), ps[r]);
+            if (!COULOMB) ps[r] = fmaf(qi, ex2_approx(c * (d2 * id)), ps[r]);
         }
     }
 }
@@ -392,8 +402,13 @@ __global__ void k_boundary_rows_f32(GridGeom g, const double *__restrict__ xyz, 
         float ps[kRowBlock], pv[kRowBlock];
 #pragma unroll
         for (int r = 0; r < kRowBlock; ++r) ps[r] = pv[r] = 0.f;
-        if (R.ft == 2) face_row_sums<true>(sa, na, w, fu, fv, c, coulomb, ps, pv);
-        else face_row_sums<false>(sa, na, w, fu, fv, c, coulomb, ps, pv);
+        if (coulomb) {
+            if (R.ft == 2) face_row_sums<true, true>(sa, na, w, fu, fv, c, ps, pv);
+            else face_row_sums<false, true>(sa, na, w, fu, fv, c, ps, pv);
+        } else {
+            if (R.ft == 2) face_row_sums<true, false>(sa, na, w, fu, fv, c, ps, pv);
+            else face_row_sums<false, false>(sa, na, w, fu, fv, c, ps, pv);
+        }
 #pragma unroll
         for (int r = 0; r < kRowBlock; ++r) {
             ss[r] += (double)(coulomb ? pv[r] : ps[r]);

@@ -272,6 +272,41 @@ __global__ void k_source_entries(const LegDev *__restrict__ legs, int n_legs) {
     }
 }
 
+// The same adds for the legs of one grid from kernel parameters: the entry count, the entry's
+// offset and charge are independent loads, then the legs' state loads, then their stores, so a
+// thread waits on two memory round trips.  Threads past the count (but inside the allocated slots)
+// load an entry slot and stop before touching a state.
+template <typename T>
+__global__ void k_source_legs(const SourceLegs S) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= S.n_slots) return;
+    const int n = *S.n_ent;
+    const int64_t p = S.ent_off[e];
+    T a;
+    if constexpr (std::is_same<T, float>::value) a = __int_as_float(S.ent_xq[e].y);
+    else a = S.ent_qt[e];
+    if (e >= n) return;
+    T v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (k < S.n_legs) v[k] = static_cast<T *>(S.u[k])[p];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (k < S.n_legs) {
+            if constexpr (std::is_same<T, float>::value) static_cast<T *>(S.u[k])[p] = fmaf(S.srcf[k], a, v[k]);
+            else static_cast<T *>(S.u[k])[p] = v[k] + S.src[k] * a;
+        }
+}
+
+cudaError_t launch_source_legs(int prec, const SourceLegs &S, cudaStream_t st) {
+    if (S.n_legs < 0 || S.n_legs > 4) return cudaErrorInvalidValue;
+    if (S.n_legs == 0 || S.n_slots < 1) return cudaSuccess;
+    const unsigned blocks = (unsigned)((S.n_slots + 255) / 256);
+    if (prec == 0) k_source_legs<double><<<blocks, 256, 0, st>>>(S);
+    else k_source_legs<float><<<blocks, 256, 0, st>>>(S);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_source_entries(int prec, const LegDev *legs, int n_legs, int n_ent_max, cudaStream_t st) {
     if (n_legs < 1 || n_ent_max < 1) return cudaSuccess;
     const unsigned blocks = (unsigned)((n_ent_max + 255) / 256);
