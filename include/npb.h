@@ -160,8 +160,9 @@ int npb_ctx_set_stream(npb_ctx *ctx, void *stream);
 /* 1: bracket every kernel launch with CUDA events and keep per-kernel totals. */
 int npb_ctx_profile(npb_ctx *ctx, int32_t enable);
 /* Per-kernel totals since profiling was enabled: for kernel class i < max_kernels,
- * names[i] (static strings), launches[i] and total device ms[i].  Returns the number
- * of classes written.  Synchronises the stream. */
+ * names[i] (static strings), launches[i] (kernel launches: a set-up class counts each kernel
+ * of its stage) and total device ms[i].  Returns the number of classes written.  Synchronises
+ * the stream. */
 int npb_ctx_kernel_stats(npb_ctx *ctx, int32_t max_kernels, const char **names,
                          int64_t *launches, double *ms);
 /* Failure-detection probe, to test the error path of the bounded device waits without a GPU

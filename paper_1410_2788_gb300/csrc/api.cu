@@ -106,13 +106,13 @@ int Profiler::begin(cudaStream_t st, cudaEvent_t *a) {
     return 0;
 }
 
-int Profiler::end(cudaStream_t st, cudaEvent_t a, int kind) {
+int Profiler::end(cudaStream_t st, cudaEvent_t a, int kind, int kernels) {
     if (!enabled) return 0;
     cudaEvent_t b;
     CU(cudaEventCreate(&b));
     CU(cudaEventRecord(b, st));
     std::lock_guard<std::mutex> lk(mu);
-    pending.push_back({a, b, kind});
+    pending.push_back({a, b, kind, kernels});
     return 0;
 }
 
@@ -122,7 +122,7 @@ int Profiler::collect() {
         CU(cudaEventSynchronize(p.b));
         float ms = 0.f;
         CU(cudaEventElapsedTime(&ms, p.a, p.b));
-        launches[p.kind] += 1;
+        launches[p.kind] += p.kernels;
         total_ms[p.kind] += ms;
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);
@@ -458,11 +458,11 @@ int npb::grid_setup(npb_grid *g, cudaStream_t st) {
     if ((rc = pr.begin(st, &ev))) return rc;
     CU(setup_mask(g->geo, g->d_xyz, g->d_rad, na, g->d_mask, g->d_half[0], g->d_half[1], g->d_half[2], g->d_mask_y,
                   g->d_mask_z, st));
-    if ((rc = pr.end(st, ev, K_SETUP_MASK))) return rc;
+    if ((rc = pr.end(st, ev, K_SETUP_MASK, na > 0 ? 2 : 1))) return rc;  // atoms' bits, transposes
     if ((rc = pr.begin(st, &ev))) return rc;
     CU(setup_charges(g->geo, g->d_xyz, g->d_q, na, g->sc, g->d_line_begin, g->d_line_count, g->d_ent_x,
                      g->d_ent_qt, g->d_ent_off, g->d_ent_xq, st));
-    if ((rc = pr.end(st, ev, K_SETUP_CHARGES))) return rc;
+    if ((rc = pr.end(st, ev, K_SETUP_CHARGES, na > 0 ? 6 : 4))) return rc;  // the charge-list build
     // face data are recomputed on their next use, only for the precision that uses them
     for (int m = 0; m < 2; ++m)
         for (int k = 0; k < 2; ++k) g->bc_valid[m][k] = false;

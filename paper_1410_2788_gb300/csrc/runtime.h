@@ -45,6 +45,7 @@ struct Profiler {
     struct Pending {
         cudaEvent_t a, b;
         int kind;
+        int kernels;  // kernel launches inside the region
     };
     bool enabled = false;
     std::mutex mu;
@@ -53,7 +54,7 @@ struct Profiler {
     double total_ms[K_COUNT] = {};
     ~Profiler();
     int begin(cudaStream_t st, cudaEvent_t *a);
-    int end(cudaStream_t st, cudaEvent_t a, int kind);
+    int end(cudaStream_t st, cudaEvent_t a, int kind, int kernels = 1);
     int collect();
 };
 
