@@ -116,3 +116,23 @@ def test_poll_timeout_and_unknown_ticket(npb):
         assert npb.npb_poll(ctx, t, 120000).status == npb.NPB_OK
     finally:
         npb.npb_ctx_destroy(ctx)
+
+
+def test_large_molecules_sharing_launches(npb):
+    """Two 8,300-atom molecules on 177^3 grids share their step launches in the serving loop; with
+    charge lists of 66,400 entry slots their source stage is a launch of its own over both grids'
+    legs (read from the leg table), where a molecule solved alone runs the by-value kernel of one
+    grid.  Both add the same FP32 product, so the energies equal the lone solves bit for bit."""
+    cases = [(I.random_walk_molecule(8300, 177, 0.5, seed=I.SEED_BASE + s),
+              npb.make_opts(0.4, 0.04, 6, precision=npb.NPB_FP32_SWEEP)) for s in (311, 312)]
+    assert all(8 * p.n_atoms >= 65536 for p, _ in cases)
+    alone = [_alone(npb, p, o) for p, o in cases]
+    ctx = npb.npb_ctx_create(0, 0)
+    try:
+        tickets = [npb.npb_submit(ctx, p, o) for p, o in cases]
+        res = [npb.npb_poll(ctx, t, 120000) for t in tickets]
+    finally:
+        npb.npb_ctx_destroy(ctx)
+    for r, ref in zip(res, alone):
+        assert r is not None and r.status == npb.NPB_OK
+        assert r.dG_kcal_mol == ref, (r.dG_kcal_mol, ref)
