@@ -16,6 +16,7 @@
 // Fused stages (flags): S (LODIE2) and N (LODIE1) on the x sweep's loaded rows, N (LODIE2) on the z
 // sweep's results.
 #include <algorithm>
+#include <type_traits>
 
 #include "npb_internal.cuh"
 #include "sweep_kernel.cuh"
@@ -200,49 +201,56 @@ __global__ void __launch_bounds__(2 * kL64Lines) k_line64_sweep(const LegDev *__
     if (!L.active) return;
     const double2 lo = xbuf[lane], hi = xbuf[kL64Lines + lane];
     const double vp = (lo.x + lo.y * hi.x) / (1.0 - lo.y * hi.y);
-    if (!upper) {
-        double v = vp;
-        u[p * st] = (post_nl && !bit(p)) ? flow(v) : v;
-        for (int k0 = p - 1; k0 >= 1; k0 -= kL64Chunk) {
-            const int nk = min(kL64Chunk, k0);
-            double w[kL64Chunk], m[kL64Chunk];
+    // back substitution; the leg's flow form (series or closed) is chosen once, outside the rows
+    auto back = [&](auto series_tag) {
+        constexpr bool SERIES = decltype(series_tag)::value;
+        auto flow_out = [&](double x) { return SERIES ? nl_flow_series(x, lg.nl_q) : nl_flow(x, lg.nl_q, lg.nl_omq); };
+        if (!upper) {
+            double v = vp;
+            u[p * st] = (post_nl && !bit(p)) ? flow_out(v) : v;
+            for (int k0 = p - 1; k0 >= 1; k0 -= kL64Chunk) {
+                const int nk = min(kL64Chunk, k0);
+                double w[kL64Chunk], m[kL64Chunk];
 #pragma unroll
-            for (int j = 0; j < kL64Chunk; ++j)
-                if (j < nk) {
-                    w[j] = u[(k0 - j) * st];
-                    m[j] = f[(k0 - j) * st];
-                }
+                for (int j = 0; j < kL64Chunk; ++j)
+                    if (j < nk) {
+                        w[j] = u[(k0 - j) * st];
+                        m[j] = f[(k0 - j) * st];
+                    }
 #pragma unroll
-            for (int j = 0; j < kL64Chunk; ++j)
-                if (j < nk) {
-                    const int k = k0 - j;
-                    const double er = l64_e(lg.rE, bit(k), bit(k + 1));
-                    v = fma(er * m[j], v, w[j]);
-                    u[k * st] = (post_nl && !bit(k)) ? flow(v) : v;
-                }
+                for (int j = 0; j < kL64Chunk; ++j)
+                    if (j < nk) {
+                        const int k = k0 - j;
+                        const double er = l64_e(lg.rE, bit(k), bit(k + 1));
+                        v = fma(er * m[j], v, w[j]);
+                        u[k * st] = (post_nl && !bit(k)) ? flow_out(v) : v;
+                    }
+            }
+        } else if (p < N) {
+            double v = fma(hi.y, vp, hi.x);
+            u[(p + 1) * st] = (post_nl && !bit(p + 1)) ? flow_out(v) : v;
+            for (int k0 = p + 2; k0 <= N; k0 += kL64Chunk) {
+                const int nk = min(kL64Chunk, N - k0 + 1);
+                double w[kL64Chunk], m[kL64Chunk];
+#pragma unroll
+                for (int j = 0; j < kL64Chunk; ++j)
+                    if (j < nk) {
+                        w[j] = u[(k0 + j) * st];
+                        m[j] = f[(k0 + j) * st];
+                    }
+#pragma unroll
+                for (int j = 0; j < kL64Chunk; ++j)
+                    if (j < nk) {
+                        const int k = k0 + j;
+                        const double el = l64_e(lg.rE, bit(k - 1), bit(k));
+                        v = fma(el * m[j], v, w[j]);
+                        u[k * st] = (post_nl && !bit(k)) ? flow_out(v) : v;
+                    }
+            }
         }
-    } else if (p < N) {
-        double v = fma(hi.y, vp, hi.x);
-        u[(p + 1) * st] = (post_nl && !bit(p + 1)) ? flow(v) : v;
-        for (int k0 = p + 2; k0 <= N; k0 += kL64Chunk) {
-            const int nk = min(kL64Chunk, N - k0 + 1);
-            double w[kL64Chunk], m[kL64Chunk];
-#pragma unroll
-            for (int j = 0; j < kL64Chunk; ++j)
-                if (j < nk) {
-                    w[j] = u[(k0 + j) * st];
-                    m[j] = f[(k0 + j) * st];
-                }
-#pragma unroll
-            for (int j = 0; j < kL64Chunk; ++j)
-                if (j < nk) {
-                    const int k = k0 + j;
-                    const double el = l64_e(lg.rE, bit(k - 1), bit(k));
-                    v = fma(el * m[j], v, w[j]);
-                    u[k * st] = (post_nl && !bit(k)) ? flow(v) : v;
-                }
-        }
-    }
+    };
+    if (post_nl && lg.nl_q <= (double)kNlSeriesMaxQ) back(std::true_type{});
+    else back(std::false_type{});
 }
 
 static dim3 l64_grid(int dir, int n_legs, int nx, int ny, int nz) {
