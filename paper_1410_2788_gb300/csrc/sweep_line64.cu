@@ -11,7 +11,8 @@
 // way up, instead of a division and the segmented elimination's bookkeeping.  GB300's FP64 units run
 // at about 1/64 of its FP32 rate, so the plain FP64 path is bound by them; fewer FP64 operations per
 // node is what speeds it up.  u is read and written in place in global memory: for y and z the 32
-// lines of a warp are x-adjacent (coalesced rows), for x each lane walks its own row.
+// lines of a warp are x-adjacent (coalesced rows); for x, whose lanes each walk their own row, the
+// rows go through shared memory in chunks copied by whole warps (k_line64_sweep_x).
 //
 // Fused stages (flags): S (LODIE2) and N (LODIE1) on the x sweep's loaded rows, N (LODIE2) on the z
 // sweep's results.
@@ -253,6 +254,162 @@ __global__ void __launch_bounds__(2 * kL64Lines) k_line64_sweep(const LegDev *__
     else back(std::false_type{});
 }
 
+// The x sweep with its rows staged through shared memory: each lane of an x sweep walks its own
+// row, so the generic kernel's loads touch 32 rows per warp instruction (latency-bound, ncu: FP64
+// pipe 34%, 46 long-scoreboard stalls per issue).  Here a warp copies a chunk of kL64Chunk rows of
+// all its 32 lines with four 64-byte row pieces per load instruction, the lanes run the recurrence
+// on the staged values, and the warp copies the results back the same way.  Same arithmetic in the
+// same order as the generic kernel (bit-identical results).  Every lane of the block takes part in
+// the copies (lines past the grid's last y line are skipped); only active lanes compute.
+__global__ void __launch_bounds__(2 * kL64Lines) k_line64_sweep_x(const LegDev *__restrict__ legs, int flags) {
+    __shared__ double2 xbuf[2 * kL64Lines];
+    __shared__ double sw[2][kL64Lines][kL64Chunk + 1], sm[2][kL64Lines][kL64Chunk + 1];
+    const LegDev &lg = legs[blockIdx.z];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const bool upper = wp == 1;
+    const int c = 1 + blockIdx.y;
+    const L64Line L = l64_line<DIR_X>(lg, blockIdx.x, c, lane);
+    const int N = lg.nx - 2, p = (N + 1) >> 1;
+    double *const ul = static_cast<double *>(lg.u) + L.base;  // this lane's row (active lanes only)
+    L64Bits bit{lg.lmask[DIR_X] ? lg.lmask[DIR_X] + L.mbase : nullptr, -1, 0u};
+    const bool nl_on = lg.nl_on != 0;
+    const bool pre_nl = (flags & FUSE_PRE_NL) && nl_on;
+    const bool pre_src = (flags & FUSE_PRE_SRC) != 0;
+
+    // rows [lo, lo + nk) of the warp's 32 lines: lane (e, lsub) copies element e of line 4 it + lsub
+    double *const ug = static_cast<double *>(lg.u);
+    const double *const fg = lg.fac[DIR_X];
+    const int y0 = 1 + blockIdx.x * kL64Lines, e = lane & 7, lsub = lane >> 3;
+    auto at = [&](int li, int row) { return ((int64_t)c * lg.ny + (y0 + li)) * lg.pitch + row; };
+    auto stage = [&](int lo, int nk) {
+#pragma unroll
+        for (int it = 0; it < kL64Lines / 4; ++it) {
+            const int li = 4 * it + lsub;
+            if (e < nk && y0 + li <= lg.ny - 2) {
+                const int64_t a = at(li, lo + e);
+                sw[wp][li][e] = ug[a];
+                sm[wp][li][e] = fg[a];
+            }
+        }
+        __syncwarp();
+    };
+    auto flush = [&](int lo, int nk) {
+        __syncwarp();
+#pragma unroll
+        for (int it = 0; it < kL64Lines / 4; ++it) {
+            const int li = 4 * it + lsub;
+            if (e < nk && y0 + li <= lg.ny - 2) ug[at(li, lo + e)] = sw[wp][li][e];
+        }
+        __syncwarp();
+    };
+    double *const w = sw[wp][lane], *const m = sm[wp][lane];
+
+    double dv = 0.0, cv = 0.0;  // (dp_p, cp_p) of the lower lane, (dq_{p+1}, aq_{p+1}) of the upper
+    if (L.active) {
+        const int r0 = upper ? p + 1 : 1, r1 = upper ? N : p;
+        if (pre_nl)  // LODIE1's N at the solvent nodes outside the molecule, before the solve
+            for (int k = r0; k <= r1; ++k)
+                if (!bit(k)) ul[k] = nl_flow_leg(ul[k], lg.nl_q, lg.nl_omq);
+        if (pre_src) {  // LODIE2's S: tau Q at this half's charge nodes of the line (y, z = c)
+            const int ln = c * lg.ny + (1 + blockIdx.x * kL64Lines + lane);
+            const int b = lg.line_begin[ln], en = b + lg.line_count[ln];
+            for (int q = b; q < en; ++q) {
+                const int x = lg.ent_x[q];
+                if (x >= r0 && x <= r1) ul[x] += lg.src * lg.ent_qt[q];
+            }
+        }
+    }
+    __syncwarp();  // the stages' writes before the copies read the rows
+    if (!upper) {
+        double el = 0.0;
+        if (L.active) {
+            dv = ul[0];  // the face u_0 enters as e_{1/2} dp_0
+            el = l64_e(lg.rE, bit(0), bit(1));
+        }
+        for (int k0 = 1; k0 <= p; k0 += kL64Chunk) {
+            const int nk = min(kL64Chunk, p - k0 + 1);
+            stage(k0, nk);
+            if (L.active) {
+#pragma unroll
+                for (int j = 0; j < kL64Chunk; ++j)
+                    if (j < nk) {
+                        const int k = k0 + j;
+                        const double er = l64_e(lg.rE, bit(k), bit(k + 1));
+                        dv = fma(el, dv, w[j]) * m[j];
+                        w[j] = dv;
+                        cv = er * m[j];
+                        el = er;
+                    }
+            }
+            flush(k0, nk);
+        }
+    } else {
+        double er = 0.0;
+        if (L.active) {
+            dv = ul[N + 1];  // u_{n-1}
+            er = l64_e(lg.rE, bit(N), bit(N + 1));
+        }
+        for (int k0 = N; k0 > p; k0 -= kL64Chunk) {
+            const int nk = min(kL64Chunk, k0 - p), lo = k0 - nk + 1;
+            stage(lo, nk);
+            if (L.active) {
+#pragma unroll
+                for (int j = 0; j < kL64Chunk; ++j)
+                    if (j < nk) {
+                        const int k = k0 - j;
+                        const double el = l64_e(lg.rE, bit(k - 1), bit(k));
+                        dv = fma(er, dv, w[k - lo]) * m[k - lo];
+                        w[k - lo] = dv;
+                        cv = el * m[k - lo];
+                        er = el;
+                    }
+            }
+            flush(lo, nk);
+        }
+    }
+    xbuf[threadIdx.x] = make_double2(dv, cv);
+    __syncthreads();
+    const double2 lo2 = xbuf[lane], hi2 = xbuf[kL64Lines + lane];
+    const double vp = (lo2.x + lo2.y * hi2.x) / (1.0 - lo2.y * hi2.y);
+    if (!upper) {
+        double v = vp;
+        if (L.active) ul[p] = v;
+        for (int k0 = p - 1; k0 >= 1; k0 -= kL64Chunk) {
+            const int nk = min(kL64Chunk, k0), lo = k0 - nk + 1;
+            stage(lo, nk);
+            if (L.active) {
+#pragma unroll
+                for (int j = 0; j < kL64Chunk; ++j)
+                    if (j < nk) {
+                        const int k = k0 - j;
+                        const double er = l64_e(lg.rE, bit(k), bit(k + 1));
+                        v = fma(er * m[k - lo], v, w[k - lo]);
+                        w[k - lo] = v;
+                    }
+            }
+            flush(lo, nk);
+        }
+    } else if (p < N) {
+        double v = fma(hi2.y, vp, hi2.x);
+        if (L.active) ul[p + 1] = v;
+        for (int k0 = p + 2; k0 <= N; k0 += kL64Chunk) {
+            const int nk = min(kL64Chunk, N - k0 + 1);
+            stage(k0, nk);
+            if (L.active) {
+#pragma unroll
+                for (int j = 0; j < kL64Chunk; ++j)
+                    if (j < nk) {
+                        const int k = k0 + j;
+                        const double el = l64_e(lg.rE, bit(k - 1), bit(k));
+                        v = fma(el * m[j], v, w[j]);
+                        w[j] = v;
+                    }
+            }
+            flush(k0, nk);
+        }
+    }
+}
+
 static dim3 l64_grid(int dir, int n_legs, int nx, int ny, int nz) {
     if (dir == DIR_X) return dim3((ny - 2 + kL64Lines - 1) / kL64Lines, nz - 2, n_legs);
     return dim3((nx - 1 + kL64Lines - 1) / kL64Lines, dir == DIR_Y ? nz - 2 : ny - 2, n_legs);
@@ -269,7 +426,7 @@ cudaError_t launch_line64_factors(int dir, const LegDev *legs, int n_legs, int n
 cudaError_t launch_sweep_line64(int dir, const LegDev *legs, int n_legs, int nx, int ny, int nz, int flags,
                                 cudaStream_t st) {
     const dim3 g = l64_grid(dir, n_legs, nx, ny, nz);
-    if (dir == DIR_X) k_line64_sweep<DIR_X><<<g, 2 * kL64Lines, 0, st>>>(legs, flags);
+    if (dir == DIR_X) k_line64_sweep_x<<<g, 2 * kL64Lines, 0, st>>>(legs, flags);
     else if (dir == DIR_Y) k_line64_sweep<DIR_Y><<<g, 2 * kL64Lines, 0, st>>>(legs, flags);
     else k_line64_sweep<DIR_Z><<<g, 2 * kL64Lines, 0, st>>>(legs, flags);
     return cudaGetLastError();
