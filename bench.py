@@ -421,7 +421,7 @@ def serving_run(npb, seconds: float, rate: float = 50.0, fifo_requests: int = 50
 
 # The sources of the FP32 interior-row sweeps (the kernels whose DRAM traffic profiles/ncu_traffic.json
 # records) and of the FP64 line sweeps.
-FP32_SWEEP_SOURCES = ("sweep_kernel.cuh", "sweep_tma.cuh", "sweep_inner.cuh", "sweep_inner_launch.cuh")
+FP32_SWEEP_SOURCES = ("sweep_kernel.cuh", "sweep_tma.cuh", "sweep_inner.cuh", "sweep_inner_launch.cuh", "f32x2.cuh")
 FP64_SWEEP_SOURCES = ("sweep_kernel.cuh", "sweep_line64.cu")
 
 

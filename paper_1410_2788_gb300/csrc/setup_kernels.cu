@@ -17,6 +17,7 @@
 
 #include "npb_internal.cuh"
 #include "setup_kernels.cuh"
+#include "f32x2.cuh"
 
 namespace npb {
 
@@ -352,26 +353,36 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
 }
 
 // FP32 pair terms of one atom chunk for a row along x (ALONG_Y false) or y; COULOMB: no screening
-// (kbar = 0), the solvent sum is the vacuum one.
+// (kbar = 0), the solvent sum is the vacuum one.  The row's two nodes go as packed pairs (one
+// instruction for both nodes' subtraction, squared distance, charge over distance, sums and
+// exponent), each lane rounded as the scalar operation; the rsqrt and exp2 stay per node.
+static_assert(kRowBlock == 2, "the packed face terms take two nodes per thread");
 template <bool ALONG_Y, bool COULOMB>
 __device__ __forceinline__ void face_row_sums(const float4 *sa, int na, const float *w, float fu, float fv, float c,
                                               float *ps, float *pv) {
+    const unsigned long long W = f2_pack(w[0], w[1]), kNeg1 = f2_pack(-1.0f, -1.0f), C = f2_pack(c, c);
+    unsigned long long PS = f2_pack(ps[0], ps[1]), PV = f2_pack(pv[0], pv[1]);
 #pragma unroll 4
     for (int t = 0; t < na; ++t) {
         const float4 P = sa[t];
         const float pw = ALONG_Y ? P.y : P.x, pu = ALONG_Y ? P.x : P.y;
         const float du = fu - pu, dv = fv - P.z;
         const float uv2 = fmaf(du, du, dv * dv);
-#pragma unroll
-        for (int r = 0; r < kRowBlock; ++r) {
-            const float dw = w[r] - pw;
-            const float d2 = fmaf(dw, dw, uv2);
-            const float id = rsqrt_approx(d2);
-            const float qi = P.w * id;
-            pv[r] += qi;
-            if (!COULOMB) ps[r] = fmaf(qi, ex2_approx(c * (d2 * id)), ps[r]);
+        const unsigned long long DW = f2_fma(f2_pack(pw, pw), kNeg1, W);  // w - pw, exactly rounded
+        const unsigned long long D2 = f2_fma(DW, DW, f2_pack(uv2, uv2));
+        float d0, d1;
+        f2_unpack(D2, d0, d1);
+        const unsigned long long ID = f2_pack(rsqrt_approx(d0), rsqrt_approx(d1));
+        const unsigned long long QI = f2_mul(f2_pack(P.w, P.w), ID);
+        PV = f2_add(PV, QI);
+        if (!COULOMB) {
+            float a0, a1;
+            f2_unpack(f2_mul(C, f2_mul(D2, ID)), a0, a1);
+            PS = f2_fma(QI, f2_pack(ex2_approx(a0), ex2_approx(a1)), PS);
         }
     }
+    f2_unpack(PS, ps[0], ps[1]);
+    f2_unpack(PV, pv[0], pv[1]);
 }
 
 // Both media's faces, FP32 pair terms (chunk sums in FP32, chunks accumulated in FP64):

@@ -20,6 +20,7 @@
 #pragma once
 #include <type_traits>
 
+#include "f32x2.cuh"
 #include "sweep_tma.cuh"
 
 namespace npb {
@@ -31,28 +32,6 @@ constexpr int kSrcRegs = 2;
 // Shared-memory stages of the tile pipeline: tile t+k*grid is in flight while tile t is solved,
 // k < kInnerStages.
 constexpr int kInnerStages = 2;
-
-// Packed FP32 pairs (sm_100 family): one instruction does two IEEE fma/mul, each lane rounded
-// exactly as the scalar operation, so results are bit-identical to the scalar code.
-__device__ __forceinline__ unsigned long long f2_pack(float a, float b) {
-    unsigned long long r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void f2_unpack(unsigned long long v, float &a, float &b) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-}
-__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
-                                                     unsigned long long c) {
-    unsigned long long d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b) {
-    unsigned long long d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
 
 // Largest PCR stride for SEG segments (the highest power of two below SEG).
 template <int SEG>
