@@ -44,10 +44,15 @@ __global__ void k_mask_atoms(GridGeom g, const double *__restrict__ xyz,
     const double r2 = __dmul_rn(rho, rho);
     const int n[3] = {g.nx, g.ny, g.nz};
     const double o[3] = {g.ox, g.oy, g.oz};
+    // The atom's node box, widened by one node on either side: any superset of the nodes within rho
+    // gives the same bits (every node is tested below), so it is estimated in FP32 with the
+    // reciprocal of h (an index off by one where the FP64 quotient lies within 1e-5 of an integer is
+    // covered by the widening), not with six FP64 divisions per thread.
+    const float ihf = 1.0f / (float)g.h;
     int lo[3], hi[3];
     for (int d = 0; d < 3; ++d) {
-        lo[d] = (int)floor((c[d] - rho - o[d]) / g.h) - 1;
-        hi[d] = (int)ceil((c[d] + rho - o[d]) / g.h) + 1;
+        lo[d] = (int)floorf((float)(c[d] - rho - o[d]) * ihf) - 1;
+        hi[d] = (int)ceilf((float)(c[d] + rho - o[d]) * ihf) + 1;
         lo[d] = max(lo[d], 0);
         hi[d] = min(hi[d], n[d] - 1);
     }
