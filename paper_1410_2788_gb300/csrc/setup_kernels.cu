@@ -17,6 +17,7 @@
 
 #include "npb_internal.cuh"
 #include "setup_kernels.cuh"
+#include "exp_table.cuh"
 #include "f32x2.cuh"
 
 namespace npb {
@@ -439,33 +440,6 @@ __global__ void k_boundary_rows_f32(GridGeom g, const double *__restrict__ xyz, 
         }
 }
 
-// exp(x) for x <= 0 by Tang's table-driven method (P. T. P. Tang, ACM TOMS 15(2), 1989), with a
-// 32-entry table: x = (32 m + j) ln2/32 + r, |r| <= ln2/64, exp(x) = 2^m 2^(j/32) exp(r), exp(r) - 1
-// by its Taylor series to r^6/720 (truncation below r^7/5040 < 4e-18).  ln2/32 is split in two
-// doubles (the second 7.2e-19) so that r carries no error from the reduction.  T[j] = 2^(j/32).
-// Arguments below -700 return 0; the result is within about 1.5 ulp (the table's rounding, the
-// final fused multiply-add and the series' rounding).
-__device__ __forceinline__ double exp_nonpos(double x, const double *T) {
-    constexpr double kInvL = 46.16624130844683;     // 32 / ln 2
-    constexpr double kL1 = 0.02166084939249829;     // ln 2 / 32, leading part
-    constexpr double kL2 = 7.247021293269686e-19;   // ln 2 / 32 - kL1
-    constexpr double kShift = 6755399441055744.0;   // 1.5 * 2^52: rounds to an integer in the low bits
-    if (x < -700.0) return 0.0;
-    const double t = fma(x, kInvL, kShift);
-    const int n = __double2loint(t);                // round(x * 32 / ln 2)
-    const double nd = t - kShift;
-    double r = fma(-nd, kL1, x);
-    r = fma(-nd, kL2, r);
-    double q = fma(r, 1.0 / 720.0, 1.0 / 120.0);
-    q = fma(q, r, 1.0 / 24.0);
-    q = fma(q, r, 1.0 / 6.0);
-    q = fma(q, r, 0.5);
-    q = fma(q, r, 1.0);
-    const double tj = T[n & 31];
-    const double e = fma(tj, r * q, tj);  // 2^(j/32) exp(r)
-    return __hiloint2double(__double2hiint(e) + (int)((unsigned)(n >> 5) << 20), __double2loint(e));
-}
-
 // FP64 pair terms of one atom chunk for a row along x (ALONG_Y false) or y, atoms in index order.
 template <bool ALONG_Y>
 __device__ __forceinline__ void face_row_sums64(const double4_32a *sa, int na, const double *w, double fu, double fv,
@@ -494,7 +468,7 @@ __global__ void k_boundary_rows_f64(GridGeom g, const double *__restrict__ xyz, 
                                     double *__restrict__ out_s, double *__restrict__ out_v) {
     __shared__ double4_32a sa[kAtomChunk];
     __shared__ double T[32];  // 2^(j/32) for exp_nonpos
-    if (threadIdx.x < 32) T[threadIdx.x] = exp2((double)threadIdx.x / 32.0);
+    exp_table_init(T);
     const FaceRow R = face_row(g.nx, g.ny, g.nz, b0, b1);
     double w[kRowBlock];
 #pragma unroll

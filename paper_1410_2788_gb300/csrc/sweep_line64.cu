@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <type_traits>
 
+#include "exp_table.cuh"
 #include "npb_internal.cuh"
 #include "sweep_kernel.cuh"
 
@@ -112,9 +113,28 @@ __global__ void __launch_bounds__(2 * kL64Lines) k_line64_factors(const LegDev *
     }
 }
 
+// The FP64 series flow of Eq. (ana3) (nl_flow_series) with exp(-|w|) - 1 from the block's exp table:
+// t = -expm1(-|w|) / (2 + expm1(-|w|)), x = q t, |w'| = 2 atanh(x) to x^15/15.  The table's rounding
+// moves t by at most 2e-14 of itself, and |w'| <= 2q, so w' is off by less than 1e-15 absolute.
+__device__ __forceinline__ double nl_flow_series_tab(double w, double q, const double *T) {
+    const double em = expm1_nonpos(-fabs(w), T);
+    const double x = q * (-em / (2.0 + em)), x2 = x * x;
+    double s = 1.0 / 15.0;
+    s = fma(s, x2, 1.0 / 13.0);
+    s = fma(s, x2, 1.0 / 11.0);
+    s = fma(s, x2, 1.0 / 9.0);
+    s = fma(s, x2, 1.0 / 7.0);
+    s = fma(s, x2, 1.0 / 5.0);
+    s = fma(s, x2, 1.0 / 3.0);
+    s = fma(s, x2, 1.0);
+    return copysign(2.0 * x * s, w);
+}
+
 template <int DIR>
 __global__ void __launch_bounds__(2 * kL64Lines) k_line64_sweep(const LegDev *__restrict__ legs, int flags) {
     __shared__ double2 xbuf[2 * kL64Lines];
+    __shared__ double T[32];  // exp table of the z sweep's nonlinear stage (visible after the xbuf barrier)
+    if (DIR == DIR_Z) exp_table_init(T);
     const LegDev &lg = legs[blockIdx.z];
     const int lane = threadIdx.x & 31;
     const bool upper = threadIdx.x >= 32;
@@ -205,7 +225,9 @@ __global__ void __launch_bounds__(2 * kL64Lines) k_line64_sweep(const LegDev *__
     // back substitution; the leg's flow form (series or closed) is chosen once, outside the rows
     auto back = [&](auto series_tag) {
         constexpr bool SERIES = decltype(series_tag)::value;
-        auto flow_out = [&](double x) { return SERIES ? nl_flow_series(x, lg.nl_q) : nl_flow(x, lg.nl_q, lg.nl_omq); };
+        auto flow_out = [&](double x) {
+            return SERIES ? nl_flow_series_tab(x, lg.nl_q, T) : nl_flow(x, lg.nl_q, lg.nl_omq);
+        };
         if (!upper) {
             double v = vp;
             u[p * st] = (post_nl && !bit(p)) ? flow_out(v) : v;
