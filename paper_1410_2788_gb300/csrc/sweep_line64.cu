@@ -130,8 +130,11 @@ __device__ __forceinline__ double nl_flow_series_tab(double w, double q, const d
     return copysign(2.0 * x * s, w);
 }
 
+// The y and z sweeps (x: k_line64_sweep_x below), reading and writing u in global memory; the 32
+// lines of a warp are x-adjacent, so every row access is coalesced.
 template <int DIR>
 __global__ void __launch_bounds__(2 * kL64Lines) k_line64_sweep(const LegDev *__restrict__ legs, int flags) {
+    static_assert(DIR == DIR_Y || DIR == DIR_Z, "the x sweep is k_line64_sweep_x");
     __shared__ double2 xbuf[2 * kL64Lines];
     __shared__ double T[32];  // exp table of the z sweep's nonlinear stage (visible after the xbuf barrier)
     if (DIR == DIR_Z) exp_table_init(T);
@@ -140,35 +143,18 @@ __global__ void __launch_bounds__(2 * kL64Lines) k_line64_sweep(const LegDev *__
     const bool upper = threadIdx.x >= 32;
     const int c = 1 + blockIdx.y;
     const L64Line L = l64_line<DIR>(lg, blockIdx.x, c, lane);
-    const int n = DIR == DIR_X ? lg.nx : (DIR == DIR_Y ? lg.ny : lg.nz);
+    const int n = DIR == DIR_Y ? lg.ny : lg.nz;
     const int N = n - 2, p = (N + 1) >> 1;
     double *u = static_cast<double *>(lg.u) + L.base;
     const double *f = lg.fac[DIR] + L.base;
     const int64_t st = L.step;
     L64Bits bit{lg.lmask[DIR] ? lg.lmask[DIR] + L.mbase : nullptr, -1, 0u};
-    const bool nl_on = lg.nl_on != 0;
-    const bool pre_nl = DIR == DIR_X && (flags & FUSE_PRE_NL) && nl_on;
-    const bool post_nl = DIR == DIR_Z && (flags & FUSE_POST_NL) && nl_on;
-    const bool pre_src = DIR == DIR_X && (flags & FUSE_PRE_SRC);
-    auto flow = [&](double v) { return nl_flow_leg(v, lg.nl_q, lg.nl_omq); };
+    const bool post_nl = DIR == DIR_Z && (flags & FUSE_POST_NL) && lg.nl_on != 0;
 
     double dv = 0.0, cv = 0.0;  // (dp_p, cp_p) of the lower thread, (dq_{p+1}, aq_{p+1}) of the upper
     if (L.active) {
-        // the rows this thread owns: 1 .. p (lower) or p+1 .. N (upper)
-        const int r0 = upper ? p + 1 : 1, r1 = upper ? N : p;
-        if (pre_nl)  // LODIE1's N at the solvent nodes outside the molecule, before the solve
-            for (int k = r0; k <= r1; ++k)
-                if (!bit(k)) u[k * st] = flow(u[k * st]);
-        if (pre_src) {  // LODIE2's S: tau Q at this half's charge nodes of the line (y, z = c)
-            const int ln = c * lg.ny + (1 + blockIdx.x * kL64Lines + lane);
-            const int b = lg.line_begin[ln], e = b + lg.line_count[ln];
-            for (int q = b; q < e; ++q) {
-                const int x = lg.ent_x[q];
-                if (x >= r0 && x <= r1) u[x * st] += lg.src * lg.ent_qt[q];
-            }
-        }
-        // rows in chunks of kL64Chunk: every chunk's loads are issued before its dependent
-        // recurrence, so the global-memory latency overlaps (each lane of an x sweep walks its own row)
+        // the rows this thread owns: 1 .. p (lower) or p+1 .. N (upper), in chunks of kL64Chunk:
+        // every chunk's loads are issued before its dependent recurrence, so the latency overlaps
         if (!upper) {
             dv = u[0];  // the face u_0 enters as e_{1/2} dp_0
             double el = l64_e(lg.rE, bit(0), bit(1));
